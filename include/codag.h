@@ -1,0 +1,193 @@
+/*
+ * codag.h - chunk-parallel GPU decompression for ORC integer RLE v1/v2 and
+ * raw Deflate (C ABI of libcodag.so, built for sm_103a).
+ *
+ * The operation (CODAG, Sec. II-B "Parallelizing Decompression"): a column
+ * is split into chunks that were compressed independently; metadata gives
+ * each chunk's compressed and uncompressed offsets, so every chunk decodes on
+ * its own.  One call decodes many chunks of one format (or, in the batch
+ * call, of mixed formats) on one GPU.  The formats are the three the paper
+ * evaluates (Sec. VI-A): ORC integer RLE version 1 and version 2 and Deflate
+ * (RFC 1951, raw: no zlib or gzip wrapper, no preset dictionary).
+ *
+ * Memory layout shared by every call (all pointers are DEVICE pointers
+ * unless noted; the caller owns every buffer):
+ *   comp          concatenated compressed chunks; must be 16-byte aligned
+ *                 (any cudaMalloc pointer is) and readable over
+ *                 [comp, comp + comp_offsets[n_chunks]).
+ *   comp_offsets  uint64[n_chunks + 1], byte offsets into comp; chunk c is
+ *                 comp[comp_offsets[c] .. comp_offsets[c+1]).  Non-decreasing.
+ *   out           output buffer; chunk c decodes into
+ *                 out[out_offsets[c] .. out_offsets[c+1]), and must fill that
+ *                 span exactly.  For the RLE formats the output is
+ *                 little-endian 64-bit integers: out must be 8-byte aligned
+ *                 and every RLE offset a multiple of 8.
+ *   out_offsets   uint64[n_chunks + 1], byte offsets into out.
+ *
+ * Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  Argument problems are reported synchronously by the
+ * return value and nothing is launched.  Problems with the DATA are reported
+ * per chunk on the device (CODAG_CHUNK_* codes below): the call still returns
+ * CODAG_OK, the bad chunk's output span is left unspecified, and the other
+ * chunks decode normally.  Per-chunk status is read with
+ * codag_last_chunk_status() (plain calls) or from the caller's chunk_status
+ * array (batch calls).  No call ever traps or faults the GPU on bad data, and
+ * every device-side wait is bounded (CODAG_CHUNK_TIMEOUT).
+ *
+ * Library-owned memory: a per-device workspace (per-chunk status of the last
+ * plain call, batch claim counter and order) allocated with cudaMalloc on
+ * first use and grown on demand; it lives until process exit.  Calls on the
+ * same device share it, so plain calls that overlap on different streams
+ * must not rely on codag_last_chunk_status().
+ */
+#ifndef CODAG_H
+#define CODAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+/* Chunk formats (CODAG Sec. VI-A).  _I64 columns are signed (ORC zigzag
+ * encoding of bases, literals and deltas as the ORC format defines), _U64
+ * unsigned. */
+typedef enum {
+  CODAG_ORC_RLE_V1_I64 = 1,
+  CODAG_ORC_RLE_V2_I64 = 2,
+  CODAG_DEFLATE_RAW = 3,
+  CODAG_ORC_RLE_V1_U64 = 4,
+  CODAG_ORC_RLE_V2_U64 = 5
+} codag_format;
+
+/* Call status (host side). */
+typedef enum {
+  CODAG_OK = 0,
+  CODAG_EINVAL = 1,   /* bad argument: pointer, alignment, format, size */
+  CODAG_ECUDA = 2,    /* a CUDA runtime call failed (see codag_last_error) */
+  CODAG_ENOMEM = 3,   /* workspace allocation failed */
+  CODAG_ECORRUPT = 4, /* reserved: returned by helpers that read statuses */
+  CODAG_ETIMEOUT = 5  /* a bounded host wait ran out */
+} codag_status;
+
+/* Per-chunk status (device side), one int32 per chunk. */
+enum {
+  CODAG_CHUNK_OK = 0,
+  CODAG_CHUNK_TRUNCATED = 1,        /* stream needs bytes past the chunk end   */
+  CODAG_CHUNK_OUTPUT_OVERFLOW = 2,  /* decodes to more than the output span   */
+  CODAG_CHUNK_OUTPUT_UNDERFLOW = 3, /* decodes to less than the output span   */
+  CODAG_CHUNK_BAD_HEADER = 4,       /* bad header, varint, block type, patch  */
+  CODAG_CHUNK_BAD_HUFFMAN = 5,      /* bad code lengths, code or symbol       */
+  CODAG_CHUNK_BAD_DISTANCE = 6,     /* back-reference before the chunk start  */
+  CODAG_CHUNK_BAD_STORED_LEN = 7,   /* Deflate stored block LEN != ~NLEN      */
+  CODAG_CHUNK_BAD_SPAN = 8,         /* offsets decrease, pass the buffer end, or
+                                       an RLE span is not a multiple of 8     */
+  CODAG_CHUNK_TIMEOUT = 9           /* a bounded device wait ran out          */
+};
+
+/*
+ * codag_decompress - decode n_chunks chunks of one format.
+ *
+ * CODAG Sec. V-C/V-D (warp-level decompression, all lanes decoding) and
+ * Sec. V-E/V-F (coalesced on-demand reading and writing): here one warp
+ * decodes one chunk, staging its compressed bytes in shared memory with 1-D
+ * TMA bulk copies and writing output with coalesced stores.
+ *
+ * format        one of codag_format.
+ * comp, comp_offsets, out, out_offsets: see the layout above (device).
+ * n_chunks      number of chunks; 0 is a no-op returning CODAG_OK.
+ * stream        CUDA stream the work is enqueued on.
+ * Returns CODAG_OK once enqueued; CODAG_EINVAL for a NULL pointer (with
+ * n_chunks > 0), an unknown format, comp not 16-byte aligned or an RLE out
+ * not 8-byte aligned; CODAG_ENOMEM / CODAG_ECUDA on runtime failure.  The
+ * per-chunk status goes to the library workspace (codag_last_chunk_status).
+ */
+codag_status codag_decompress(int format, const void *comp, const uint64_t *comp_offsets,
+                              uint64_t n_chunks, void *out, const uint64_t *out_offsets,
+                              cudaStream_t stream);
+
+/*
+ * codag_decompressed_sizes - decoded size in bytes of each chunk.
+ *
+ * Chunked formats normally carry uncompressed offsets (CODAG Sec. II-B); this
+ * query recovers them when they are missing.  RLE v1/v2 walk the stream
+ * without storing values (cheap); raw Deflate stores no size, so the Deflate
+ * query decodes every symbol without writing output (about the cost of a
+ * decode).  sizes_out: device uint64[n_chunks], written asynchronously.  A
+ * chunk that fails to decode gets its size up to the error and a non-zero
+ * status in the workspace (codag_last_chunk_status).  Returns as
+ * codag_decompress (sizes_out must be non-NULL).
+ */
+codag_status codag_decompressed_sizes(int format, const void *comp, const uint64_t *comp_offsets,
+                                      uint64_t n_chunks, uint64_t *sizes_out,
+                                      cudaStream_t stream);
+
+/*
+ * codag_decompress_batch - decode a batch of chunks of mixed formats in one
+ * persistent, work-stealing launch (CODAG Sec. II-B chunk parallelism; the
+ * batching itself is this library's, not the paper's).
+ *
+ * formats       device uint8[n_chunks], a codag_format per chunk (an unknown
+ *               value marks that chunk CODAG_CHUNK_BAD_HEADER).
+ * chunk_status  device int32[n_chunks] for per-chunk status, or NULL to use
+ *               the library workspace (codag_last_chunk_status).
+ * Other arguments as codag_decompress.  Chunks are claimed largest first
+ * (by log2 of compressed + uncompressed bytes).  The enqueued work is a
+ * memset, two small ordering kernels and the persistent decode kernel; it
+ * allocates nothing once the workspace is large enough, so it may be
+ * captured into a CUDA graph after one warm-up call of at least this size.
+ */
+codag_status codag_decompress_batch(const uint8_t *formats, const void *comp,
+                                    const uint64_t *comp_offsets, uint64_t n_chunks, void *out,
+                                    const uint64_t *out_offsets, int32_t *chunk_status,
+                                    cudaStream_t stream);
+
+/*
+ * codag_last_chunk_status - copy the per-chunk status of the last plain call
+ * (codag_decompress, codag_decompressed_sizes, or a batch call without
+ * chunk_status) on the current device into host_status[0..n).  Synchronises
+ * `stream`.  host_status is HOST memory.  Returns CODAG_EINVAL if n exceeds
+ * the last call's chunk count, CODAG_ECORRUPT (after copying) if any chunk is
+ * not CODAG_CHUNK_OK.
+ */
+codag_status codag_last_chunk_status(int32_t *host_status, uint64_t n, cudaStream_t stream);
+
+/*
+ * A batch decode captured once into a CUDA graph and replayed.  create
+ * captures codag_decompress_batch for fixed arguments (all pointers stay
+ * owned by the caller and must outlive the graph) with a private claim
+ * counter and order buffer, so several graphs may run concurrently.
+ * chunk_status must be non-NULL.  launch enqueues one replay on `stream`.
+ */
+typedef struct codag_graph_s *codag_graph;
+codag_status codag_batch_graph_create(const uint8_t *formats, const void *comp,
+                                      const uint64_t *comp_offsets, uint64_t n_chunks, void *out,
+                                      const uint64_t *out_offsets, int32_t *chunk_status,
+                                      cudaStream_t stream, codag_graph *graph_out);
+codag_status codag_batch_graph_launch(codag_graph graph, cudaStream_t stream);
+codag_status codag_batch_graph_destroy(codag_graph graph);
+
+/*
+ * Launch shape of the persistent batch kernel: resident CTAs (4 decoder
+ * warps each) per SM.  0 = as many as fit (the default).  Used by the
+ * autotuner; takes effect for later calls and graph captures.
+ */
+codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm);
+int codag_get_batch_ctas_per_sm(void);
+
+/* Number of kernel launches the library enqueued since load (all calls). */
+uint64_t codag_kernel_launches(void);
+
+/* Human-readable text of the last error on this thread ("" if none). */
+const char *codag_last_error(void);
+
+/* Library version, e.g. "codag-gb300 0.1". */
+const char *codag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CODAG_H */

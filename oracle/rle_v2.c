@@ -29,8 +29,9 @@
  *   - a patch-list entry is PGW + PW bits rounded up to the next encodable
  *     width (the "closest fixed bits" rule of the ORC writers); PGW + PW > 64
  *     is BAD_HEADER; an entry with gap 255 and patch 0 only advances the
- *     position by 255; a patch position at or past L is BAD_HEADER; a filler
- *     run that reaches the end of the list adds no patch;
+ *     position by 255; patch positions must stay below L and strictly
+ *     increase (a gap of 0 after a patch would patch one value twice), else
+ *     BAD_HEADER; a filler run that reaches the end of the list adds no patch;
  *   - a DELTA run with W != 0 and L = 1 yields only the base;
  *   - padding bits are ignored.
  * Error order within a run: header and field problems in stream order, then
@@ -158,14 +159,17 @@ int oracle_rle_v2(const uint8_t *in, size_t n_in, int is_signed,
         int ew = v2_closest_fixed_bits(pgw + pw);
         if ((st = v2_unpack(&s, (size_t)pll, ew, entries)) != ORC_OK) return st;
         /* walk the patch list: positions accumulate gaps from 0 */
-        size_t pos = 0;
+        uint64_t pos = 0, prev = 0;
+        int have_prev = 0;
         for (int e = 0; e < pll; e++) {
-          uint64_t gap = pw == 64 ? 0 : entries[e] >> pw;
-          uint64_t patch = pw == 64 ? entries[e] : entries[e] & (((uint64_t)1 << pw) - 1);
-          pos += (size_t)gap;
+          uint64_t gap = entries[e] >> pw; /* pw <= 63: pgw >= 1 and pgw + pw <= 64 */
+          uint64_t patch = entries[e] & (((uint64_t)1 << pw) - 1);
+          pos += gap;
           if (gap == 255 && patch == 0) continue; /* filler entry */
-          if (pos >= len) return ORC_BAD_HEADER;
+          if (pos >= len || (have_prev && pos <= prev)) return ORC_BAD_HEADER;
           vals[pos] |= w == 64 ? 0 : patch << w;
+          prev = pos;
+          have_prev = 1;
         }
         for (size_t i = 0; i < len; i++) vals[i] = base + vals[i];
       } else { /* DELTA */

@@ -1,0 +1,191 @@
+"""Python binding of libcodag.so: chunk-parallel GPU decompression of ORC
+integer RLE v1/v2 and raw Deflate on one GB300 (CODAG, arXiv 2307.03760).
+
+Argument marshalling only: every decoding step runs in the CUDA kernels
+behind the C ABI declared in ``include/codag.h``; the functions here carry
+the same names and turn torch tensors (device memory) and torch streams into
+the raw pointers and stream handles the ABI takes.  There is no CPU path: if
+the compiled library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+CODAG_ORC_RLE_V1_I64 = 1
+CODAG_ORC_RLE_V2_I64 = 2
+CODAG_DEFLATE_RAW = 3
+CODAG_ORC_RLE_V1_U64 = 4
+CODAG_ORC_RLE_V2_U64 = 5
+FORMATS = {"rle_v1": 1, "rle_v2": 2, "deflate": 3, "rle_v1_u64": 4, "rle_v2_u64": 5}
+
+CODAG_OK, CODAG_EINVAL, CODAG_ECUDA, CODAG_ENOMEM, CODAG_ECORRUPT, CODAG_ETIMEOUT = range(6)
+CHUNK_STATUS = ["OK", "TRUNCATED", "OUTPUT_OVERFLOW", "OUTPUT_UNDERFLOW", "BAD_HEADER",
+                "BAD_HUFFMAN", "BAD_DISTANCE", "BAD_STORED_LEN", "BAD_SPAN", "TIMEOUT"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class CodagError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcodag.so (building it first when nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not _build.up_to_date():
+            try:
+                _build.build()
+            except Exception as e:  # no silent fallback: the GPU library is the product
+                raise RuntimeError(f"libcodag.so is missing and could not be built: {e}") from e
+        L = ctypes.CDLL(_build.LIB_PATH)
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        L.codag_decompress.argtypes = [i32, vp, vp, u64, vp, vp, vp]
+        L.codag_decompressed_sizes.argtypes = [i32, vp, vp, u64, vp, vp]
+        L.codag_decompress_batch.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
+        L.codag_last_chunk_status.argtypes = [vp, u64, vp]
+        L.codag_batch_graph_create.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.codag_batch_graph_launch.argtypes = [vp, vp]
+        L.codag_batch_graph_destroy.argtypes = [vp]
+        L.codag_set_batch_ctas_per_sm.argtypes = [i32]
+        for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
+                     "codag_last_chunk_status", "codag_batch_graph_create",
+                     "codag_batch_graph_launch", "codag_batch_graph_destroy",
+                     "codag_set_batch_ctas_per_sm"):
+            getattr(L, name).restype = i32
+        L.codag_get_batch_ctas_per_sm.restype = i32
+        L.codag_kernel_launches.restype = ctypes.c_uint64
+        L.codag_last_error.restype = ctypes.c_char_p
+        L.codag_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st: int, where: str):
+    if st != CODAG_OK:
+        raise CodagError(st, where, lib().codag_last_error().decode())
+
+
+def _fmt(f) -> int:
+    return FORMATS[f] if isinstance(f, str) else int(f)
+
+
+def codag_decompress(fmt, comp, comp_offsets, n_chunks: int, out, out_offsets, stream=None):
+    """Decode n_chunks chunks of one format (device tensors or raw pointers)."""
+    _check(lib().codag_decompress(_fmt(fmt), _ptr(comp), _ptr(comp_offsets), n_chunks, _ptr(out),
+                                  _ptr(out_offsets), _stream(stream)), "codag_decompress")
+
+
+def codag_decompressed_sizes(fmt, comp, comp_offsets, n_chunks: int, sizes_out, stream=None):
+    _check(lib().codag_decompressed_sizes(_fmt(fmt), _ptr(comp), _ptr(comp_offsets), n_chunks,
+                                          _ptr(sizes_out), _stream(stream)),
+           "codag_decompressed_sizes")
+
+
+def codag_decompress_batch(formats, comp, comp_offsets, n_chunks: int, out, out_offsets,
+                           chunk_status=None, stream=None):
+    _check(lib().codag_decompress_batch(_ptr(formats), _ptr(comp), _ptr(comp_offsets), n_chunks,
+                                        _ptr(out), _ptr(out_offsets), _ptr(chunk_status),
+                                        _stream(stream)), "codag_decompress_batch")
+
+
+def codag_last_chunk_status(n: int, stream=None):
+    """Per-chunk status of the last plain call as a numpy int32 array."""
+    import numpy as np
+    host = np.zeros(max(n, 1), dtype=np.int32)
+    st = lib().codag_last_chunk_status(host.ctypes.data, n, _stream(stream))
+    if st not in (CODAG_OK, CODAG_ECORRUPT):
+        _check(st, "codag_last_chunk_status")
+    return host[:n]
+
+
+class BatchGraph:
+    """codag_batch_graph_create/launch/destroy as an object."""
+
+    def __init__(self, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
+                 stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().codag_batch_graph_create(_ptr(formats), _ptr(comp), _ptr(comp_offsets),
+                                              n_chunks, _ptr(out), _ptr(out_offsets),
+                                              _ptr(chunk_status), _stream(stream),
+                                              ctypes.byref(h)), "codag_batch_graph_create")
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().codag_batch_graph_launch(self._h, _stream(stream)), "codag_batch_graph_launch")
+
+    def destroy(self):
+        if self._h:
+            lib().codag_batch_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def codag_batch_graph_create(*args, **kw) -> BatchGraph:
+    return BatchGraph(*args, **kw)
+
+
+def codag_batch_graph_launch(graph: BatchGraph, stream=None):
+    graph.launch(stream)
+
+
+def codag_batch_graph_destroy(graph: BatchGraph):
+    graph.destroy()
+
+
+def codag_set_batch_ctas_per_sm(k: int):
+    _check(lib().codag_set_batch_ctas_per_sm(int(k)), "codag_set_batch_ctas_per_sm")
+
+
+def codag_get_batch_ctas_per_sm() -> int:
+    return lib().codag_get_batch_ctas_per_sm()
+
+
+def codag_kernel_launches() -> int:
+    return lib().codag_kernel_launches()
+
+
+def codag_version() -> str:
+    return lib().codag_version().decode()
+
+
+# short aliases
+decompress = codag_decompress
+decompressed_sizes = codag_decompressed_sizes
+decompress_batch = codag_decompress_batch
+last_chunk_status = codag_last_chunk_status

@@ -1,0 +1,356 @@
+// Host side of the C ABI (include/codag.h): argument checks, the per-device
+// workspace, kernel launches and the batch graph.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/codag.h"
+#include "kernels.cuh"
+
+using namespace codag;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_batch_ctas_per_sm{0};
+
+codag_status fail(codag_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+codag_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(CODAG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kMaxDevices = 64;
+
+struct Workspace {
+  int32_t* status = nullptr;     // per-chunk status of the last plain call
+  uint64_t status_cap = 0;
+  uint64_t last_n = 0;
+  uint32_t* order = nullptr;     // batch claim order
+  uint64_t order_cap = 0;
+  uint32_t* counters = nullptr;  // [0] claim counter, [1..64] hist, [65..128] cursor
+  bool attrs_set = false;
+  int sm_count = 0;
+};
+
+std::mutex g_mu;
+Workspace g_ws[kMaxDevices];
+
+codag_status current_ws(Workspace** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(CODAG_EINVAL, "device index out of range");
+  Workspace& w = g_ws[dev];
+  if (!w.attrs_set) {
+    const int bytes[] = {kWarpsPerBlock * kRleV1Warp, kWarpsPerBlock * kRleV2Warp,
+                         kWarpsPerBlock * kDeflateWarp, kWarpsPerBlock * kBatchWarp};
+    const void* fns[] = {(const void*)rle_v1_kernel,  (const void*)rle_v1_sizes_kernel,
+                         (const void*)rle_v2_kernel,  (const void*)rle_v2_sizes_kernel,
+                         (const void*)inflate_kernel, (const void*)inflate_sizes_kernel,
+                         (const void*)batch_kernel};
+    const int which[] = {0, 0, 1, 1, 2, 2, 3};
+    for (int i = 0; i < 7; i++) {
+      e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[which[i]]);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    e = cudaMalloc(&w.counters, 129 * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(CODAG_ENOMEM, "workspace allocation failed");
+    w.attrs_set = true;
+  }
+  *out = &w;
+  return CODAG_OK;
+}
+
+codag_status grow_status(Workspace& w, uint64_t n) {
+  if (n <= w.status_cap) return CODAG_OK;
+  if (w.status) cudaFree(w.status);
+  w.status = nullptr;
+  w.status_cap = 0;
+  uint64_t cap = n < 1024 ? 1024 : n + n / 4;
+  if (cudaMalloc(&w.status, cap * sizeof(int32_t)) != cudaSuccess)
+    return fail(CODAG_ENOMEM, "status workspace allocation failed");
+  w.status_cap = cap;
+  return CODAG_OK;
+}
+
+codag_status grow_order(Workspace& w, uint64_t n) {
+  if (n <= w.order_cap) return CODAG_OK;
+  if (w.order) cudaFree(w.order);
+  w.order = nullptr;
+  w.order_cap = 0;
+  uint64_t cap = n < 1024 ? 1024 : n + n / 4;
+  if (cudaMalloc(&w.order, cap * sizeof(uint32_t)) != cudaSuccess)
+    return fail(CODAG_ENOMEM, "order workspace allocation failed");
+  w.order_cap = cap;
+  return CODAG_OK;
+}
+
+bool is_rle(int f) {
+  return f == CODAG_ORC_RLE_V1_I64 || f == CODAG_ORC_RLE_V1_U64 || f == CODAG_ORC_RLE_V2_I64 ||
+         f == CODAG_ORC_RLE_V2_U64;
+}
+int family_of(int f) {
+  if (f == CODAG_ORC_RLE_V1_I64 || f == CODAG_ORC_RLE_V1_U64) return 1;
+  if (f == CODAG_ORC_RLE_V2_I64 || f == CODAG_ORC_RLE_V2_U64) return 2;
+  if (f == CODAG_DEFLATE_RAW) return 3;
+  return 0;
+}
+
+codag_status check_common(const void* comp, const uint64_t* comp_offsets, uint64_t n) {
+  if (!comp || !comp_offsets) return fail(CODAG_EINVAL, "NULL comp or comp_offsets");
+  if (reinterpret_cast<uintptr_t>(comp) & 15) return fail(CODAG_EINVAL, "comp must be 16-byte aligned");
+  if (n > (1ull << 32) - 1) return fail(CODAG_EINVAL, "too many chunks (max 2^32 - 1)");
+  return CODAG_OK;
+}
+
+codag_status launch_plain(int format, const void* comp, const uint64_t* comp_offsets, uint64_t n,
+                          void* out, const uint64_t* out_offsets, uint64_t* sizes, bool store,
+                          cudaStream_t stream) {
+  const int fam = family_of(format);
+  if (!fam) return fail(CODAG_EINVAL, "unknown format");
+  if (n == 0) return CODAG_OK;
+  codag_status s = check_common(comp, comp_offsets, n);
+  if (s != CODAG_OK) return s;
+  if (store) {
+    if (!out || !out_offsets) return fail(CODAG_EINVAL, "NULL out or out_offsets");
+    if (is_rle(format) && (reinterpret_cast<uintptr_t>(out) & 7))
+      return fail(CODAG_EINVAL, "RLE out must be 8-byte aligned");
+  } else if (!sizes) {
+    return fail(CODAG_EINVAL, "NULL sizes_out");
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  if ((s = current_ws(&w)) != CODAG_OK) return s;
+  if ((s = grow_status(*w, n)) != CODAG_OK) return s;
+  w->last_n = n;
+  Args a{};
+  a.comp = static_cast<const uint8_t*>(comp);
+  a.comp_off = comp_offsets;
+  a.n = n;
+  a.out = static_cast<uint8_t*>(out);
+  a.out_off = out_offsets;
+  a.sizes = sizes;
+  a.status = w->status;
+  a.format = format;
+  const unsigned grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  const int per_warp = fam == 1 ? kRleV1Warp : fam == 2 ? kRleV2Warp : kDeflateWarp;
+  const size_t smem = (size_t)kWarpsPerBlock * per_warp;
+  const void* fn;
+  if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
+  else if (fam == 2) fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
+  else fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
+  void* params[] = {&a};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), params, smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+  g_launches.fetch_add(1);
+  return CODAG_OK;
+}
+
+// Enqueue the batch path with the given scratch (status, order, counters).
+codag_status enqueue_batch(const Workspace& w, const uint8_t* formats, const void* comp,
+                           const uint64_t* comp_offsets, uint64_t n, void* out,
+                           const uint64_t* out_offsets, int32_t* status, uint32_t* order,
+                           uint32_t* counters, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counters, 0, 129 * sizeof(uint32_t), stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  const unsigned og = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+  order_hist_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n, counters + 1);
+  order_scatter_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n, counters + 1,
+                                               counters + 65, order);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "order launch");
+  Args a{};
+  a.comp = static_cast<const uint8_t*>(comp);
+  a.comp_off = comp_offsets;
+  a.n = n;
+  a.out = static_cast<uint8_t*>(out);
+  a.out_off = out_offsets;
+  a.status = status;
+  a.formats = formats;
+  a.order = order;
+  a.counter = counters;
+  const size_t smem = (size_t)kWarpsPerBlock * kBatchWarp;
+  int fit = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, kThreads, smem);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  int per_sm = g_batch_ctas_per_sm.load();
+  if (per_sm <= 0 || per_sm > fit) per_sm = fit;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)per_sm * (uint64_t)w.sm_count;
+  const uint64_t need = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (grid > need) grid = need;
+  batch_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  g_launches.fetch_add(3);
+  return CODAG_OK;
+}
+
+codag_status check_batch(const uint8_t* formats, const void* comp, const uint64_t* comp_offsets,
+                         uint64_t n, void* out, const uint64_t* out_offsets) {
+  codag_status s = check_common(comp, comp_offsets, n);
+  if (s != CODAG_OK) return s;
+  if (!formats || !out || !out_offsets) return fail(CODAG_EINVAL, "NULL formats, out or out_offsets");
+  if (reinterpret_cast<uintptr_t>(out) & 7) return fail(CODAG_EINVAL, "out must be 8-byte aligned");
+  return CODAG_OK;
+}
+
+}  // namespace
+
+struct codag_graph_s {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  uint32_t* order = nullptr;
+  uint32_t* counters = nullptr;
+};
+
+extern "C" {
+
+codag_status codag_decompress(int format, const void* comp, const uint64_t* comp_offsets,
+                              uint64_t n_chunks, void* out, const uint64_t* out_offsets,
+                              cudaStream_t stream) {
+  return launch_plain(format, comp, comp_offsets, n_chunks, out, out_offsets, nullptr, true, stream);
+}
+
+codag_status codag_decompressed_sizes(int format, const void* comp, const uint64_t* comp_offsets,
+                                      uint64_t n_chunks, uint64_t* sizes_out, cudaStream_t stream) {
+  return launch_plain(format, comp, comp_offsets, n_chunks, nullptr, nullptr, sizes_out, false,
+                      stream);
+}
+
+codag_status codag_decompress_batch(const uint8_t* formats, const void* comp,
+                                    const uint64_t* comp_offsets, uint64_t n_chunks, void* out,
+                                    const uint64_t* out_offsets, int32_t* chunk_status,
+                                    cudaStream_t stream) {
+  if (n_chunks == 0) return CODAG_OK;
+  codag_status s = check_batch(formats, comp, comp_offsets, n_chunks, out, out_offsets);
+  if (s != CODAG_OK) return s;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  if ((s = current_ws(&w)) != CODAG_OK) return s;
+  if ((s = grow_order(*w, n_chunks)) != CODAG_OK) return s;
+  if (!chunk_status) {
+    if ((s = grow_status(*w, n_chunks)) != CODAG_OK) return s;
+    w->last_n = n_chunks;
+    chunk_status = w->status;
+  }
+  return enqueue_batch(*w, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
+                       w->order, w->counters, stream);
+}
+
+codag_status codag_last_chunk_status(int32_t* host_status, uint64_t n, cudaStream_t stream) {
+  if (n == 0) return CODAG_OK;
+  if (!host_status) return fail(CODAG_EINVAL, "NULL host_status");
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  codag_status s;
+  if ((s = current_ws(&w)) != CODAG_OK) return s;
+  if (n > w->last_n || !w->status) return fail(CODAG_EINVAL, "n exceeds the last call's chunk count");
+  cudaError_t e = cudaMemcpyAsync(host_status, w->status, n * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  for (uint64_t i = 0; i < n; i++)
+    if (host_status[i] != CODAG_CHUNK_OK) return CODAG_ECORRUPT;
+  return CODAG_OK;
+}
+
+codag_status codag_batch_graph_create(const uint8_t* formats, const void* comp,
+                                      const uint64_t* comp_offsets, uint64_t n_chunks, void* out,
+                                      const uint64_t* out_offsets, int32_t* chunk_status,
+                                      cudaStream_t stream, codag_graph* graph_out) {
+  if (!graph_out) return fail(CODAG_EINVAL, "NULL graph_out");
+  *graph_out = nullptr;
+  if (n_chunks == 0 || !chunk_status) return fail(CODAG_EINVAL, "n_chunks == 0 or NULL chunk_status");
+  codag_status s = check_batch(formats, comp, comp_offsets, n_chunks, out, out_offsets);
+  if (s != CODAG_OK) return s;
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  if ((s = current_ws(&w)) != CODAG_OK) return s;
+  codag_graph g = new codag_graph_s();
+  if (cudaMalloc(&g->order, n_chunks * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&g->counters, 129 * sizeof(uint32_t)) != cudaSuccess) {
+    if (g->order) cudaFree(g->order);
+    delete g;
+    return fail(CODAG_ENOMEM, "graph scratch allocation failed");
+  }
+  cudaStream_t cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(g->order);
+    cudaFree(g->counters);
+    delete g;
+    return cuda_fail(e, "capture stream");
+  }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const uint64_t before = g_launches.load();
+    s = enqueue_batch(*w, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
+                      g->order, g->counters, cap);
+    g_launches.store(before);  // captured, not launched
+    cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
+    if (s == CODAG_OK && e2 != cudaSuccess) s = cuda_fail(e2, "end capture");
+    if (s == CODAG_OK) {
+      e2 = cudaGraphInstantiate(&g->exec, g->graph, 0);
+      if (e2 != cudaSuccess) s = cuda_fail(e2, "graph instantiate");
+    }
+  } else {
+    s = cuda_fail(e, "begin capture");
+  }
+  cudaStreamDestroy(cap);
+  (void)stream;
+  if (s != CODAG_OK) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->order);
+    cudaFree(g->counters);
+    delete g;
+    return s;
+  }
+  *graph_out = g;
+  return CODAG_OK;
+}
+
+codag_status codag_batch_graph_launch(codag_graph graph, cudaStream_t stream) {
+  if (!graph || !graph->exec) return fail(CODAG_EINVAL, "NULL graph");
+  cudaError_t e = cudaGraphLaunch(graph->exec, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  g_launches.fetch_add(3);
+  return CODAG_OK;
+}
+
+codag_status codag_batch_graph_destroy(codag_graph graph) {
+  if (!graph) return CODAG_OK;
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  if (graph->order) cudaFree(graph->order);
+  if (graph->counters) cudaFree(graph->counters);
+  delete graph;
+  return CODAG_OK;
+}
+
+codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm) {
+  if (ctas_per_sm < 0 || ctas_per_sm > 64) return fail(CODAG_EINVAL, "ctas_per_sm out of range");
+  g_batch_ctas_per_sm.store(ctas_per_sm);
+  return CODAG_OK;
+}
+
+int codag_get_batch_ctas_per_sm(void) { return g_batch_ctas_per_sm.load(); }
+
+uint64_t codag_kernel_launches(void) { return g_launches.load(); }
+
+const char* codag_last_error(void) { return g_last_error.c_str(); }
+
+const char* codag_version(void) { return "codag-gb300 0.1"; }
+
+}  // extern "C"

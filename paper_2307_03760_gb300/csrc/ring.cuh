@@ -1,0 +1,151 @@
+// Per-decoder input staging ring (CODAG Sec. V-E, "coalesced on-demand
+// reading": a warp refills an input buffer with whole cache lines when it has
+// room, and decoding then reads from the buffer).
+//
+// GB300 form: the ring is NSLOT slots of SLOT bytes in shared memory.  Each
+// slot is filled by one 1-D TMA bulk copy (cp.async.bulk, 16-byte aligned
+// source and size) issued by lane 0 and completed on the slot's mbarrier; the
+// ragged tail (< 16 bytes at the end of the readable range) is fetched with
+// plain byte loads.  Refills are issued up to NSLOT slots ahead of the lowest
+// position the decoder still needs, so the next slots are in flight while the
+// current one is decoded.  Every lane keeps an identical copy of the ring
+// state, like every other piece of decoder state.
+//
+// Positions are chunk-relative byte offsets.  Ring position r = chunk
+// position + skew, where skew (0..15) aligns ring position 0 to 16 bytes.
+// ensure(lo, hi) makes chunk bytes [lo, hi) resident and releases every slot
+// below lo; hi - lo must not exceed (NSLOT - 1) * SLOT.  Bytes past the end
+// of the readable range are never fetched: reads there return stale data and
+// the decoders bound every read by the chunk length themselves.
+#pragma once
+
+#include "common.cuh"
+
+namespace codag {
+
+template <int SLOT_, int NSLOT_>
+struct InRing {
+  static constexpr int SLOT = SLOT_;
+  static constexpr int NSLOT = NSLOT_;
+  static constexpr int BYTES = SLOT * NSLOT;
+  static constexpr int MAX_SPAN = (NSLOT - 1) * SLOT;
+  static_assert((SLOT & (SLOT - 1)) == 0 && SLOT >= 64, "slot: power of two >= 64");
+  static_assert((NSLOT & (NSLOT - 1)) == 0 && NSLOT >= 2, "nslot: power of two >= 2");
+  // shared memory this ring needs: data + one mbarrier per slot
+  static constexpr int SMEM = BYTES + 8 * NSLOT;
+
+  uint8_t* buf;        // shared, BYTES, 128-byte aligned
+  uint64_t* bar;       // shared, NSLOT mbarriers
+  const uint8_t* gsrc; // 16-byte aligned global address of ring position 0
+  int64_t skew;        // chunk start - gsrc
+  int64_t limit;       // readable ring positions: [0, limit)
+  uint32_t issued;     // slots issued for this chunk
+  uint32_t ready;      // slots waited for (in order)
+  uint32_t parity;     // per-slot mbarrier phase parity (persists across chunks)
+
+  // Once per warp: carve the ring out of `smem` and initialise barriers.
+  __device__ __forceinline__ void init(uint8_t* smem) {
+    buf = smem;
+    bar = reinterpret_cast<uint64_t*>(smem + BYTES);
+    parity = 0;
+    if (lane_id() == 0) {
+      for (int s = 0; s < NSLOT; s++) mbar_init(&bar[s], 1);
+      fence_mbar_init();
+      fence_proxy_async_smem();
+    }
+    __syncwarp();
+  }
+
+  // Start a chunk of `len` bytes at `chunk`; `buf_end` bounds every read.
+  __device__ __forceinline__ void start(const uint8_t* chunk, int64_t len, const uint8_t* buf_end) {
+    gsrc = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(chunk) & ~uintptr_t(15));
+    skew = chunk - gsrc;
+    int64_t lim = (skew + len + 15) & ~int64_t(15);
+    int64_t hard = buf_end - gsrc;
+    limit = lim < hard ? lim : hard;
+    issued = 0;
+    ready = 0;
+  }
+
+  __device__ __forceinline__ void issue_next() {
+    const uint32_t k = issued;
+    const int s = k & (NSLOT - 1);
+    const int64_t off = (int64_t)k * SLOT;
+    int64_t bytes = limit - off;
+    if (bytes > SLOT) bytes = SLOT;
+    if (bytes > 0) {
+      const uint32_t bulk = (uint32_t)bytes & ~15u;
+      const uint32_t tail = (uint32_t)bytes - bulk;
+      if (lane_id() == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bar[s], bulk);
+        if (bulk) tma_load_1d(buf + s * SLOT, gsrc + off, bulk, &bar[s]);
+      }
+      if (lane_id() < tail) buf[s * SLOT + bulk + lane_id()] = __ldg(gsrc + off + bulk + lane_id());
+    }
+    issued = k + 1;
+  }
+
+  // Wait for slot `ready`; false if the bounded wait ran out.
+  __device__ __forceinline__ bool wait_next() {
+    const uint32_t k = ready;
+    const int s = k & (NSLOT - 1);
+    if ((int64_t)k * SLOT < limit) {
+      if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u)) return false;
+      parity ^= 1u << s;
+    }
+    ready = k + 1;
+    return true;
+  }
+
+  // Make chunk bytes [lo, hi) resident, release slots below lo and keep up to
+  // NSLOT slots in flight.  False on a wait timeout.
+  __device__ __forceinline__ bool ensure(int64_t lo, int64_t hi) {
+    const int64_t rhi = hi + skew;
+    if (rhi <= (int64_t)ready * SLOT) return true;
+    __syncwarp();  // every lane's reads of released slots precede their refill
+    const uint32_t k_lo = (uint32_t)((lo + skew) / SLOT);
+    const uint32_t k_hi = (uint32_t)((rhi + SLOT - 1) / SLOT);
+    while (issued < k_lo + NSLOT && (int64_t)issued * SLOT < limit) {
+      // the buffer slot being refilled must have been waited for first
+      while (ready + NSLOT <= issued)
+        if (!wait_next()) return false;
+      issue_next();
+    }
+    while (ready < k_hi) {
+      if (ready >= issued) {  // past the readable range: nothing to wait for
+        ready = k_hi;
+        break;
+      }
+      if (!wait_next()) return false;
+    }
+    __syncwarp();
+    return true;
+  }
+
+  // Wait for every copy still in flight (end of a chunk).
+  __device__ __forceinline__ bool drain() {
+    while (ready < issued)
+      if (!wait_next()) return false;
+    __syncwarp();
+    return true;
+  }
+
+  __device__ __forceinline__ const uint8_t* chunk_ptr() const { return gsrc + skew; }
+
+  // --- reads (chunk positions; the bytes must be resident) ---------------
+  __device__ __forceinline__ uint8_t byte(int64_t p) const {
+    return buf[(uint32_t)(p + skew) & (BYTES - 1)];
+  }
+  // 8 bytes starting at p, little-endian (byte p in bits 0..7)
+  __device__ __forceinline__ uint64_t u64(int64_t p) const {
+    const uint32_t r = (uint32_t)(p + skew);
+    const uint32_t a = r & ~7u;
+    const uint32_t sh = (r & 7u) * 8;
+    const uint64_t lo = *reinterpret_cast<const uint64_t*>(buf + (a & (BYTES - 1)));
+    const uint64_t hi = *reinterpret_cast<const uint64_t*>(buf + ((a + 8) & (BYTES - 1)));
+    return (lo >> sh) | ((hi << 1) << (63 - sh));
+  }
+};
+
+}  // namespace codag

@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares; argument checks that need no GPU return EINVAL."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_2307_03760_gb300 as codag
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(codag_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for required in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
+                     "codag_last_chunk_status"):
+        assert required in names
+
+
+@pytest.mark.parametrize("name", declared_functions())
+def test_library_exports(name):
+    L = codag.lib()
+    assert hasattr(L, name), f"{name} declared in include/ but not exported"
+
+
+def test_library_is_in_tree():
+    assert os.path.realpath(codag.library_path()).startswith(os.path.realpath(ROOT))
+
+
+def test_version():
+    assert codag.codag_version().startswith("codag-gb300")
+
+
+def test_argument_errors_without_gpu():
+    L = codag.lib()
+    # unknown format, checked before any CUDA call
+    assert L.codag_decompress(42, None, None, 0, None, None, None) == codag.CODAG_EINVAL
+    # zero chunks is a no-op
+    assert L.codag_decompress(1, None, None, 0, None, None, None) == codag.CODAG_OK
+    # NULL comp with chunks
+    assert L.codag_decompress(1, None, None, 5, None, None, None) == codag.CODAG_EINVAL
+    # misaligned comp pointer (never dereferenced)
+    assert L.codag_decompress(3, 0x1001, 0x2000, 5, 0x3000, 0x4000, None) == codag.CODAG_EINVAL
+    # misaligned RLE output
+    assert L.codag_decompress(1, 0x1000, 0x2000, 5, 0x3004, 0x4000, None) == codag.CODAG_EINVAL
+    assert L.codag_decompressed_sizes(2, 0x1000, 0x2000, 5, None, None) == codag.CODAG_EINVAL
+    assert L.codag_decompress_batch(None, 0x1000, 0x2000, 5, 0x3000, 0x4000, None, None) == codag.CODAG_EINVAL
+    assert L.codag_set_batch_ctas_per_sm(-1) == codag.CODAG_EINVAL
+    assert b"aligned" in L.codag_last_error() or b"NULL" in L.codag_last_error() or L.codag_last_error()
+    assert L.codag_batch_graph_launch(None, None) == codag.CODAG_EINVAL
+
+
+def test_python_binding_names_match_abi():
+    for name in declared_functions():
+        if name in ("codag_last_error",):
+            continue
+        assert hasattr(codag, name), f"binding lacks {name}"
