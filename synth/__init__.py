@@ -182,14 +182,15 @@ def deflate_column(seed: int = 1, total: int = 1 * GiB, chunk: int = 64 * 1024, 
 
 def batched_plan(seed: int = 1, n_chunks: int = 20000, lo: int = 4096, hi: int = MiB):
     """Mixed batch plan: 40% RLE v2, 20% RLE v1, 40% Deflate; sizes
-    log-uniform in [lo, hi) (RLE rounded down to a multiple of 8)."""
+    log-uniform in [lo, hi), rounded down to a multiple of 8 so that every
+    chunk's output offset suits the 8-byte RLE values."""
     g = np.random.Generator(np.random.PCG64(seed * 7919 + 4))
     u = g.integers(0, 100, n_chunks)
     fmts = np.where(u < 40, RLE_V2_I64, np.where(u < 60, RLE_V1_I64, DEFLATE)).astype(np.uint8)
     lo_oct, hi_oct = int(np.log2(lo)), int(np.log2(hi))
     octave = g.integers(lo_oct, hi_oct, n_chunks)
     sizes = (np.left_shift(1, octave) + g.integers(0, 1 << 62, n_chunks) % np.left_shift(1, octave))
-    sizes = np.where(fmts == DEFLATE, sizes, sizes // 8 * 8).astype(np.int64)
+    sizes = (sizes // 8 * 8).astype(np.int64)
     return fmts, sizes
 
 
