@@ -156,6 +156,33 @@ codag_status codag_decompress_batch(const uint8_t *formats, const void *comp,
 codag_status codag_last_chunk_status(int32_t *host_status, uint64_t n, cudaStream_t stream);
 
 /*
+ * codag_decompress_batch_noalloc - the batch decode above, for callers that
+ * cannot let a library allocate device memory: programs that budget or pool
+ * every byte of device memory themselves, and latency-critical loops that
+ * cannot afford the device-wide synchronisation a first-call cudaMalloc may
+ * cause.  The paper has no counterpart; this is an interface choice of this
+ * library.
+ *
+ * It allocates nothing.  Its scratch (claim counter, size histogram, claim
+ * order) is a fixed array compiled into the library, so every GPU that loads
+ * the library holds it (about 257 KiB) until the process exits.  At most
+ * CODAG_NOALLOC_MAX_CHUNKS chunks per call: a larger n_chunks returns
+ * CODAG_EINVAL and enqueues nothing.  chunk_status (device int32[n_chunks])
+ * is required; the other arguments are those of codag_decompress_batch.
+ * The first call on each device does a one-time set-up (it looks up the
+ * array's device address and sets the kernel's shared-memory limit) with
+ * that device current; make that first call before any stream capture.
+ * Every call on a device shares the one array: each call clears what must
+ * start at zero, but calls whose work overlaps on the GPU (for example on
+ * two streams) race on it, so issue them one after another.
+ */
+#define CODAG_NOALLOC_MAX_CHUNKS 65536
+codag_status codag_decompress_batch_noalloc(const uint8_t *formats, const void *comp,
+                                            const uint64_t *comp_offsets, uint64_t n_chunks,
+                                            void *out, const uint64_t *out_offsets,
+                                            int32_t *chunk_status, cudaStream_t stream);
+
+/*
  * A batch decode captured once into a CUDA graph and replayed.  create
  * captures codag_decompress_batch for fixed arguments (all pointers stay
  * owned by the caller and must outlive the graph) with a private claim

@@ -57,6 +57,7 @@ def lib() -> ctypes.CDLL:
         L.codag_decompressed_sizes.argtypes = [i32, vp, vp, u64, vp, vp]
         L.codag_decompress_batch.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
         L.codag_last_chunk_status.argtypes = [vp, u64, vp]
+        L.codag_decompress_batch_noalloc.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
         L.codag_batch_graph_create.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp, ctypes.POINTER(vp)]
         L.codag_batch_graph_launch.argtypes = [vp, vp]
         L.codag_batch_graph_destroy.argtypes = [vp]
@@ -64,7 +65,7 @@ def lib() -> ctypes.CDLL:
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
                      "codag_last_chunk_status", "codag_batch_graph_create",
                      "codag_batch_graph_launch", "codag_batch_graph_destroy",
-                     "codag_set_batch_ctas_per_sm"):
+                     "codag_set_batch_ctas_per_sm", "codag_decompress_batch_noalloc"):
             getattr(L, name).restype = i32
         L.codag_get_batch_ctas_per_sm.restype = i32
         L.codag_kernel_launches.restype = ctypes.c_uint64
@@ -117,6 +118,20 @@ def codag_decompress_batch(formats, comp, comp_offsets, n_chunks: int, out, out_
     _check(lib().codag_decompress_batch(_ptr(formats), _ptr(comp), _ptr(comp_offsets), n_chunks,
                                         _ptr(out), _ptr(out_offsets), _ptr(chunk_status),
                                         _stream(stream)), "codag_decompress_batch")
+
+
+def codag_decompress_batch_noalloc(formats, comp, comp_offsets, n_chunks: int, out, out_offsets,
+                                   chunk_status, stream=None):
+    """Batch decode that allocates no device memory (scratch is a fixed array
+    in the library, at most CODAG_NOALLOC_MAX_CHUNKS chunks per call; calls
+    must not overlap on the GPU).  chunk_status is required."""
+    _check(lib().codag_decompress_batch_noalloc(_ptr(formats), _ptr(comp), _ptr(comp_offsets),
+                                                n_chunks, _ptr(out), _ptr(out_offsets),
+                                                _ptr(chunk_status), _stream(stream)),
+           "codag_decompress_batch_noalloc")
+
+
+CODAG_NOALLOC_MAX_CHUNKS = 65536
 
 
 def codag_last_chunk_status(n: int, stream=None):

@@ -206,6 +206,12 @@ codag_status check_batch(const uint8_t* formats, const void* comp, const uint64_
 
 }  // namespace
 
+namespace codag {
+// For entry points defined in other translation units.
+void note_launches(uint64_t n) { g_launches.fetch_add(n); }
+void note_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace codag
+
 struct codag_graph_s {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;

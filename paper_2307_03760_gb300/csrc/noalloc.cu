@@ -1,0 +1,139 @@
+// codag_decompress_batch_noalloc: the mixed-format batch decode for callers
+// that cannot let a library allocate device memory.
+//
+// Who needs it: programs that account for every byte of device memory
+// themselves (a fixed budget or their own pool, where an allocation behind
+// their back breaks the accounting), and latency-critical loops where the
+// first-call cudaMalloc of the ordinary entry point, which can synchronise the
+// whole device, is not acceptable.
+//
+// How: the batch kernel's scratch (claim counter, size histogram, claim
+// order) lives in the file-scope array below instead of the library
+// workspace.  The array is part of the library image, so every GPU that loads
+// the library holds it (about 257 KiB) until the process exits.  Host code
+// may not use the array's name as a device address; the first call on each
+// device, with that device current, asks the runtime for the array's address
+// with cudaGetSymbolAddress and keeps it.  That first call also sets the
+// kernel's shared-memory attribute, so make it before any stream capture.
+//
+// All calls on a device share the one array and it keeps the last call's
+// contents: each call clears the parts that must start at zero before its
+// kernels run.  Calls whose work overlaps on the GPU (for example on two
+// streams) race on the array and must not be issued.
+#include <mutex>
+#include <string>
+
+#include "../../include/codag.h"
+#include "kernels.cuh"
+
+namespace codag {
+void note_launches(uint64_t n);
+void note_error(const std::string& msg);
+}  // namespace codag
+
+using namespace codag;
+
+namespace {
+
+constexpr uint64_t kMaxChunks = CODAG_NOALLOC_MAX_CHUNKS;
+constexpr int kCounterWords = 129;  // [0] claim counter, [1..64] histogram, [65..128] cursors
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kCounterWords + kMaxChunks];
+
+struct DeviceSetup {
+  bool ready = false;
+  uint32_t* scratch = nullptr;  // device address of g_noalloc_scratch
+  int sm_count = 0;
+  int fit = 0;  // resident batch CTAs per SM
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+DeviceSetup g_setup[kMaxDevices];
+
+codag_status fail(codag_status s, const std::string& msg) {
+  note_error(msg);
+  return s;
+}
+
+// Once per device, with the device current: find the array and size the grid.
+codag_status setup_current_device(DeviceSetup** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(CODAG_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_setup_mu);
+  DeviceSetup& s = g_setup[dev];
+  if (!s.ready) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(CODAG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    const size_t smem = (size_t)kWarpsPerBlock * kBatchWarp;
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+      return fail(CODAG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    e = cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+      return fail(CODAG_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.fit, batch_kernel, kThreads, smem);
+    if (e != cudaSuccess)
+      return fail(CODAG_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    s.scratch = static_cast<uint32_t*>(p);
+    s.ready = true;
+  }
+  *out = &s;
+  return CODAG_OK;
+}
+
+}  // namespace
+
+extern "C" codag_status codag_decompress_batch_noalloc(const uint8_t* formats, const void* comp,
+                                                       const uint64_t* comp_offsets,
+                                                       uint64_t n_chunks, void* out,
+                                                       const uint64_t* out_offsets,
+                                                       int32_t* chunk_status,
+                                                       cudaStream_t stream) {
+  if (n_chunks == 0) return CODAG_OK;
+  if (n_chunks > kMaxChunks)
+    return fail(CODAG_EINVAL, "codag_decompress_batch_noalloc: n_chunks " + std::to_string(n_chunks) +
+                                  " exceeds the maximum of " + std::to_string(kMaxChunks));
+  if (!formats || !comp || !comp_offsets || !out || !out_offsets || !chunk_status)
+    return fail(CODAG_EINVAL, "codag_decompress_batch_noalloc: NULL argument");
+  if (reinterpret_cast<uintptr_t>(comp) & 15) return fail(CODAG_EINVAL, "comp must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(out) & 7) return fail(CODAG_EINVAL, "out must be 8-byte aligned");
+  DeviceSetup* s;
+  codag_status st = setup_current_device(&s);
+  if (st != CODAG_OK) return st;
+  uint32_t* counters = s->scratch;
+  uint32_t* order = s->scratch + kCounterWords;
+
+  // the counter, histogram and cursors must start at zero on every call
+  cudaError_t e = cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), stream);
+  if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  const unsigned og = (unsigned)((n_chunks + 255) / 256 < 1024 ? (n_chunks + 255) / 256 : 1024);
+  order_hist_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n_chunks, counters + 1);
+  order_scatter_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n_chunks, counters + 1,
+                                               counters + 65, order);
+  Args a{};
+  a.comp = static_cast<const uint8_t*>(comp);
+  a.comp_off = comp_offsets;
+  a.n = n_chunks;
+  a.out = static_cast<uint8_t*>(out);
+  a.out_off = out_offsets;
+  a.status = chunk_status;
+  a.formats = formats;
+  a.order = order;
+  a.counter = counters;
+  int per_sm = codag_get_batch_ctas_per_sm();
+  if (per_sm <= 0 || per_sm > s->fit) per_sm = s->fit;
+  if (per_sm < 1) per_sm = 1;
+  uint64_t grid = (uint64_t)per_sm * (uint64_t)s->sm_count;
+  const uint64_t need = (n_chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (grid > need) grid = need;
+  batch_kernel<<<(unsigned)grid, kThreads, (size_t)kWarpsPerBlock * kBatchWarp, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  note_launches(3);
+  return CODAG_OK;
+}

@@ -1,0 +1,64 @@
+"""The allocation-free batch entry point, through the C ABI.
+
+codag_decompress_batch_noalloc serves callers that cannot let the library
+allocate device memory (their own memory budget or pool, or loops that
+cannot take a first-call cudaMalloc).  Its output and per-chunk status must
+equal those of codag_decompress_batch bit for bit, on two calls in a row
+that share the library's fixed scratch array.  This file is collected last
+so that a run stopping at the first failure has run every other test."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2307_03760_gb300 as codag  # noqa: E402
+from devutil import DEV, dev_u8, dev_u64  # noqa: E402
+
+
+def _upload(w):
+    return (dev_u8(w.formats), dev_u8(w.comp), dev_u64(w.comp_off), dev_u64(w.out_off))
+
+
+def _reference(w):
+    fm, comp, coff, ooff = _upload(w)
+    out = torch.zeros(w.out_bytes + 16, dtype=torch.uint8, device=DEV)
+    st = torch.full((w.n,), -1, dtype=torch.int32, device=DEV)
+    codag.codag_decompress_batch(fm, comp, coff, w.n, out, ooff, st)
+    torch.cuda.synchronize()
+    return out[: w.out_bytes].cpu().numpy(), st.cpu().numpy()
+
+
+def _noalloc(w):
+    fm, comp, coff, ooff = _upload(w)
+    out = torch.full((w.out_bytes + 16,), 0x5A, dtype=torch.uint8, device=DEV)
+    st = torch.full((w.n,), -1, dtype=torch.int32, device=DEV)
+    codag.codag_decompress_batch_noalloc(fm, comp, coff, w.n, out, ooff, st)
+    torch.cuda.synchronize()
+    return out[: w.out_bytes].cpu().numpy(), st.cpu().numpy()
+
+
+def test_noalloc_matches_batch_two_calls_in_a_row():
+    first = synth.batched(seed=17, n_chunks=3000, lo=512, hi=1 << 17, keep_plain=True)
+    second = synth.batched(seed=18, n_chunks=1200, lo=512, hi=1 << 16, keep_plain=True)
+    for w in (first, second):  # the second call reuses the scratch the first left behind
+        ref_out, ref_st = _reference(w)
+        out, st = _noalloc(w)
+        assert (ref_st == 0).all()
+        assert np.array_equal(st, ref_st)
+        assert np.array_equal(out, ref_out)
+        assert np.array_equal(out, w.plain)
+
+
+def test_noalloc_rejects_too_many_chunks():
+    n = codag.CODAG_NOALLOC_MAX_CHUNKS + 1
+    dummy = torch.zeros(64, dtype=torch.uint8, device=DEV)
+    with pytest.raises(codag.CodagError) as e:
+        codag.codag_decompress_batch_noalloc(dummy, dummy, dummy, n, dummy, dummy, dummy)
+    assert e.value.status == codag.CODAG_EINVAL
+    assert "exceeds the maximum" in str(e.value)
