@@ -197,15 +197,18 @@ def oracle_rate(w, fmt: int, seconds: float = 10.0, threads: int | None = None):
     return done / el / 1e9, threads, reps, el
 
 
+SCALE = 1.0  # workload size factor (profiling captures use smaller cases)
+
+
 def workload(name: str, seed: int):
     if name == "rle_v1":
-        return synth.rle_v1_column(seed)
+        return synth.rle_v1_column(seed, total=int(8 * synth.MiB * SCALE) // 65536 * 65536 or 65536)
     if name == "rle_v2":
-        return synth.rle_v2_column(seed)
+        return synth.rle_v2_column(seed, total=int(256 * synth.MiB * SCALE) // 131072 * 131072 or 131072)
     if name == "deflate":
-        return synth.deflate_column(seed)
+        return synth.deflate_column(seed, total=int(synth.GiB * SCALE) // 65536 * 65536 or 65536)
     if name == "batched":
-        return synth.batched(seed)
+        return synth.batched(seed, n_chunks=max(1, int(20000 * SCALE)))
     raise ValueError(name)
 
 
@@ -286,7 +289,13 @@ def main():
     ap.add_argument("--workload", default="rle_v2", choices=list(WORKLOAD_DESC))
     ap.add_argument("--no-per-format", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--parts", type=int, default=0,
+                    help="parts per RLE chunk (0 = library default)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="workload size factor; 1.0 is the measured configuration")
     args = ap.parse_args()
+    global SCALE
+    SCALE = args.scale
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
 
@@ -306,6 +315,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     codag.lib()
+    if args.parts:
+        codag.codag_set_parts_per_chunk(args.parts)
     stream = torch.cuda.current_stream()
     peak, peak_kind = hbm_peak()
 
@@ -378,10 +389,11 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64" if name in ("rle_v1", "rle_v2") else "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[name], "chunks": w.n, "compressed_bytes": w.comp_bytes,
+        "config": {"workload": WORKLOAD_DESC[name] + ("" if SCALE == 1.0 else f"_scaled_{SCALE}"), "chunks": w.n, "compressed_bytes": w.comp_bytes,
                    "uncompressed_bytes": w.out_bytes, "ratio": round(w.comp_bytes / w.out_bytes, 4),
                    "l2": "inputs+outputs larger than L2 (no flush)", "seed": 1,
-                   "parallelism": f"chunk-parallel x{world} (independent columns per GPU)"},
+                   "parallelism": f"chunk-parallel x{world} (independent columns per GPU)",
+                   "parts_per_chunk": codag.codag_get_parts_per_chunk() or "auto"},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": w.comp_bytes + 16 * (w.n + 1),
                 "d2h_bytes_per_step": w.out_bytes, "output_checked": bool(ok)},

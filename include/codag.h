@@ -135,8 +135,10 @@ codag_status codag_decompressed_sizes(int format, const void *comp, const uint64
  * chunk_status  device int32[n_chunks] for per-chunk status, or NULL to use
  *               the library workspace (codag_last_chunk_status).
  * Other arguments as codag_decompress.  Chunks are claimed largest first
- * (by log2 of compressed + uncompressed bytes).  The enqueued work is a
- * memset, two small ordering kernels and the persistent decode kernel; it
+ * (by log2 of compressed + uncompressed bytes); an RLE chunk of 2^b bytes
+ * (compressed + decoded) is split into clamp(2^(b-16), 1, 16) parts decoded
+ * by different warps.  The enqueued work is two memsets, two small ordering
+ * kernels, the persistent decode kernel and a status-combining kernel; it
  * allocates nothing once the workspace is large enough, so it may be
  * captured into a CUDA graph after one warm-up call of at least this size.
  */
@@ -164,8 +166,9 @@ codag_status codag_last_chunk_status(int32_t *host_status, uint64_t n, cudaStrea
  * library.
  *
  * It allocates nothing.  Its scratch (claim counter, size histogram, claim
- * order) is a fixed array compiled into the library, so every GPU that loads
- * the library holds it (about 257 KiB) until the process exits.  At most
+ * order, combined status of split chunks) is a fixed array compiled into the
+ * library, so every GPU that loads the library holds it (about 385 KiB)
+ * until the process exits.  At most
  * CODAG_NOALLOC_MAX_CHUNKS chunks per call: a larger n_chunks returns
  * CODAG_EINVAL and enqueues nothing.  chunk_status (device int32[n_chunks])
  * is required; the other arguments are those of codag_decompress_batch.
@@ -176,7 +179,7 @@ codag_status codag_last_chunk_status(int32_t *host_status, uint64_t n, cudaStrea
  * start at zero, but calls whose work overlaps on the GPU (for example on
  * two streams) race on it, so issue them one after another.
  */
-#define CODAG_NOALLOC_MAX_CHUNKS 65536
+#define CODAG_NOALLOC_MAX_CHUNKS 32768
 codag_status codag_decompress_batch_noalloc(const uint8_t *formats, const void *comp,
                                             const uint64_t *comp_offsets, uint64_t n_chunks,
                                             void *out, const uint64_t *out_offsets,
@@ -204,6 +207,17 @@ codag_status codag_batch_graph_destroy(codag_graph graph);
  */
 codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm);
 int codag_get_batch_ctas_per_sm(void);
+
+/*
+ * Parts per chunk for the plain RLE calls (codag_decompress with an RLE
+ * format): one CTA per chunk runs this many warps, each decoding the runs
+ * that start in its share of the chunk's output values (every warp walks the
+ * run headers before its share).  0 = automatic (the default: the smallest
+ * power of two that gives at least 32 warps per SM, at most 16); otherwise a
+ * power of two <= 16.  Used by the autotuner.
+ */
+codag_status codag_set_parts_per_chunk(int parts);
+int codag_get_parts_per_chunk(void);
 
 /* Number of kernel launches the library enqueued since load (all calls). */
 uint64_t codag_kernel_launches(void);

@@ -62,10 +62,13 @@ def lib() -> ctypes.CDLL:
         L.codag_batch_graph_launch.argtypes = [vp, vp]
         L.codag_batch_graph_destroy.argtypes = [vp]
         L.codag_set_batch_ctas_per_sm.argtypes = [i32]
+        L.codag_set_parts_per_chunk.argtypes = [i32]
+        L.codag_get_parts_per_chunk.restype = i32
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
                      "codag_last_chunk_status", "codag_batch_graph_create",
                      "codag_batch_graph_launch", "codag_batch_graph_destroy",
-                     "codag_set_batch_ctas_per_sm", "codag_decompress_batch_noalloc"):
+                     "codag_set_batch_ctas_per_sm", "codag_decompress_batch_noalloc",
+                     "codag_set_parts_per_chunk"):
             getattr(L, name).restype = i32
         L.codag_get_batch_ctas_per_sm.restype = i32
         L.codag_kernel_launches.restype = ctypes.c_uint64
@@ -131,7 +134,7 @@ def codag_decompress_batch_noalloc(formats, comp, comp_offsets, n_chunks: int, o
            "codag_decompress_batch_noalloc")
 
 
-CODAG_NOALLOC_MAX_CHUNKS = 65536
+CODAG_NOALLOC_MAX_CHUNKS = 32768
 
 
 def codag_last_chunk_status(n: int, stream=None):
@@ -189,6 +192,14 @@ def codag_set_batch_ctas_per_sm(k: int):
 
 def codag_get_batch_ctas_per_sm() -> int:
     return lib().codag_get_batch_ctas_per_sm()
+
+
+def codag_set_parts_per_chunk(k: int):
+    _check(lib().codag_set_parts_per_chunk(int(k)), "codag_set_parts_per_chunk")
+
+
+def codag_get_parts_per_chunk() -> int:
+    return lib().codag_get_parts_per_chunk()
 
 
 def codag_kernel_launches() -> int:

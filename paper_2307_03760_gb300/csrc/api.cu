@@ -16,6 +16,7 @@ namespace {
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_batch_ctas_per_sm{0};
+std::atomic<int> g_parts_per_chunk{0};
 
 codag_status fail(codag_status s, const std::string& msg) {
   g_last_error = msg;
@@ -33,8 +34,9 @@ struct Workspace {
   uint64_t status_cap = 0;
   uint64_t last_n = 0;
   uint32_t* order = nullptr;     // batch claim order
+  unsigned long long* keys = nullptr;  // batch combined status of multi-part chunks
   uint64_t order_cap = 0;
-  uint32_t* counters = nullptr;  // [0] claim counter, [1..64] hist, [65..128] cursor
+  uint32_t* counters = nullptr;  // kBatchCounterWords words
   bool attrs_set = false;
   int sm_count = 0;
 };
@@ -49,20 +51,23 @@ codag_status current_ws(Workspace** out) {
   if (dev < 0 || dev >= kMaxDevices) return fail(CODAG_EINVAL, "device index out of range");
   Workspace& w = g_ws[dev];
   if (!w.attrs_set) {
-    const int bytes[] = {kWarpsPerBlock * kRleV1Warp, kWarpsPerBlock * kRleV2Warp,
-                         kWarpsPerBlock * kDeflateWarp, kWarpsPerBlock * kBatchWarp};
-    const void* fns[] = {(const void*)rle_v1_kernel,  (const void*)rle_v1_sizes_kernel,
-                         (const void*)rle_v2_kernel,  (const void*)rle_v2_sizes_kernel,
-                         (const void*)inflate_kernel, (const void*)inflate_sizes_kernel,
-                         (const void*)batch_kernel};
-    const int which[] = {0, 0, 1, 1, 2, 2, 3};
-    for (int i = 0; i < 7; i++) {
-      e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes[which[i]]);
+    struct {
+      const void* fn;
+      int bytes;
+    } attrs[] = {{(const void*)rle_v1_kernel, kRleMaxSmem},
+                 {(const void*)rle_v1_sizes_kernel, kRleMaxSmem},
+                 {(const void*)rle_v2_kernel, kRleMaxSmem},
+                 {(const void*)rle_v2_sizes_kernel, kRleMaxSmem},
+                 {(const void*)inflate_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)batch_kernel, kBatchSmem}};
+    for (auto& at : attrs) {
+      e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, at.bytes);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-    e = cudaMalloc(&w.counters, 129 * sizeof(uint32_t));
+    e = cudaMalloc(&w.counters, kBatchCounterWords * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(CODAG_ENOMEM, "workspace allocation failed");
     w.attrs_set = true;
   }
@@ -85,10 +90,13 @@ codag_status grow_status(Workspace& w, uint64_t n) {
 codag_status grow_order(Workspace& w, uint64_t n) {
   if (n <= w.order_cap) return CODAG_OK;
   if (w.order) cudaFree(w.order);
+  if (w.keys) cudaFree(w.keys);
   w.order = nullptr;
+  w.keys = nullptr;
   w.order_cap = 0;
   uint64_t cap = n < 1024 ? 1024 : n + n / 4;
-  if (cudaMalloc(&w.order, cap * sizeof(uint32_t)) != cudaSuccess)
+  if (cudaMalloc(&w.order, cap * sizeof(uint32_t)) != cudaSuccess ||
+      cudaMalloc(&w.keys, cap * sizeof(unsigned long long)) != cudaSuccess)
     return fail(CODAG_ENOMEM, "order workspace allocation failed");
   w.order_cap = cap;
   return CODAG_OK;
@@ -141,31 +149,50 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   a.sizes = sizes;
   a.status = w->status;
   a.format = format;
-  const unsigned grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  const int per_warp = fam == 1 ? kRleV1Warp : fam == 2 ? kRleV2Warp : kDeflateWarp;
-  const size_t smem = (size_t)kWarpsPerBlock * per_warp;
   const void* fn;
-  if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
-  else if (fam == 2) fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
-  else fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
+  unsigned grid, block;
+  size_t smem;
+  if (fam == 3) {
+    grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    block = kThreads;
+    smem = (size_t)kWarpsPerBlock * kDeflateWarp;
+    fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
+  } else {
+    // parts per chunk: enough warps to fill the GPU, at most 16 per chunk
+    int parts = g_parts_per_chunk.load();
+    if (!store) parts = 1;
+    if (parts <= 0) {
+      parts = 1;
+      while (parts < 16 && (uint64_t)parts * n < (uint64_t)w->sm_count * 32) parts *= 2;
+    }
+    grid = (unsigned)n;
+    block = 32u * (unsigned)parts;
+    int stage = kRleStageBytes;
+    if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;  // ring fallback fits
+    a.stage_bytes = stage;
+    smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
+    if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
+    else fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
+  }
   void* params[] = {&a};
-  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), params, smem, stream);
+  cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   g_launches.fetch_add(1);
   return CODAG_OK;
 }
 
-// Enqueue the batch path with the given scratch (status, order, counters).
+// Enqueue the batch path with the given scratch (status, order, keys, counters).
 codag_status enqueue_batch(const Workspace& w, const uint8_t* formats, const void* comp,
                            const uint64_t* comp_offsets, uint64_t n, void* out,
                            const uint64_t* out_offsets, int32_t* status, uint32_t* order,
-                           uint32_t* counters, cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(counters, 0, 129 * sizeof(uint32_t), stream);
+                           unsigned long long* keys, uint32_t* counters, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(counters, 0, kBatchCounterWords * sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, n * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   const unsigned og = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
-  order_hist_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n, counters + 1);
-  order_scatter_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n, counters + 1,
-                                               counters + 65, order);
+  order_hist_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n, counters + 1);
+  order_scatter_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n,
+                                               counters + 1, counters + 1 + kBuckets, order);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "order launch");
   Args a{};
@@ -178,20 +205,19 @@ codag_status enqueue_batch(const Workspace& w, const uint8_t* formats, const voi
   a.formats = formats;
   a.order = order;
   a.counter = counters;
-  const size_t smem = (size_t)kWarpsPerBlock * kBatchWarp;
+  a.keys = keys;
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, kThreads, kBatchSmem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   int per_sm = g_batch_ctas_per_sm.load();
   if (per_sm <= 0 || per_sm > fit) per_sm = fit;
   if (per_sm < 1) per_sm = 1;
-  uint64_t grid = (uint64_t)per_sm * (uint64_t)w.sm_count;
-  const uint64_t need = (n + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (grid > need) grid = need;
-  batch_kernel<<<(unsigned)grid, kThreads, smem, stream>>>(a);
+  const uint64_t grid = (uint64_t)per_sm * (uint64_t)w.sm_count;
+  batch_kernel<<<(unsigned)grid, kThreads, kBatchSmem, stream>>>(a);
+  batch_finalize_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n, keys, status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
-  g_launches.fetch_add(3);
+  g_launches.fetch_add(4);
   return CODAG_OK;
 }
 
@@ -216,6 +242,7 @@ struct codag_graph_s {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   uint32_t* order = nullptr;
+  unsigned long long* keys = nullptr;
   uint32_t* counters = nullptr;
 };
 
@@ -250,7 +277,7 @@ codag_status codag_decompress_batch(const uint8_t* formats, const void* comp,
     chunk_status = w->status;
   }
   return enqueue_batch(*w, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
-                       w->order, w->counters, stream);
+                       w->order, w->keys, w->counters, stream);
 }
 
 codag_status codag_last_chunk_status(int32_t* host_status, uint64_t n, cudaStream_t stream) {
@@ -285,8 +312,10 @@ codag_status codag_batch_graph_create(const uint8_t* formats, const void* comp,
   if ((s = current_ws(&w)) != CODAG_OK) return s;
   codag_graph g = new codag_graph_s();
   if (cudaMalloc(&g->order, n_chunks * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&g->counters, 129 * sizeof(uint32_t)) != cudaSuccess) {
+      cudaMalloc(&g->keys, n_chunks * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&g->counters, kBatchCounterWords * sizeof(uint32_t)) != cudaSuccess) {
     if (g->order) cudaFree(g->order);
+    if (g->keys) cudaFree(g->keys);
     delete g;
     return fail(CODAG_ENOMEM, "graph scratch allocation failed");
   }
@@ -294,6 +323,7 @@ codag_status codag_batch_graph_create(const uint8_t* formats, const void* comp,
   cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaFree(g->order);
+    cudaFree(g->keys);
     cudaFree(g->counters);
     delete g;
     return cuda_fail(e, "capture stream");
@@ -302,7 +332,7 @@ codag_status codag_batch_graph_create(const uint8_t* formats, const void* comp,
   if (e == cudaSuccess) {
     const uint64_t before = g_launches.load();
     s = enqueue_batch(*w, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
-                      g->order, g->counters, cap);
+                      g->order, g->keys, g->counters, cap);
     g_launches.store(before);  // captured, not launched
     cudaError_t e2 = cudaStreamEndCapture(cap, &g->graph);
     if (s == CODAG_OK && e2 != cudaSuccess) s = cuda_fail(e2, "end capture");
@@ -319,6 +349,7 @@ codag_status codag_batch_graph_create(const uint8_t* formats, const void* comp,
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     cudaFree(g->order);
+    cudaFree(g->keys);
     cudaFree(g->counters);
     delete g;
     return s;
@@ -331,7 +362,7 @@ codag_status codag_batch_graph_launch(codag_graph graph, cudaStream_t stream) {
   if (!graph || !graph->exec) return fail(CODAG_EINVAL, "NULL graph");
   cudaError_t e = cudaGraphLaunch(graph->exec, stream);
   if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-  g_launches.fetch_add(3);
+  g_launches.fetch_add(4);
   return CODAG_OK;
 }
 
@@ -340,6 +371,7 @@ codag_status codag_batch_graph_destroy(codag_graph graph) {
   if (graph->exec) cudaGraphExecDestroy(graph->exec);
   if (graph->graph) cudaGraphDestroy(graph->graph);
   if (graph->order) cudaFree(graph->order);
+  if (graph->keys) cudaFree(graph->keys);
   if (graph->counters) cudaFree(graph->counters);
   delete graph;
   return CODAG_OK;
@@ -352,6 +384,15 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm) {
 }
 
 int codag_get_batch_ctas_per_sm(void) { return g_batch_ctas_per_sm.load(); }
+
+codag_status codag_set_parts_per_chunk(int parts) {
+  if (parts < 0 || parts > 16 || (parts & (parts - 1)))
+    return fail(CODAG_EINVAL, "parts per chunk must be 0 or a power of two <= 16");
+  g_parts_per_chunk.store(parts);
+  return CODAG_OK;
+}
+
+int codag_get_parts_per_chunk(void) { return g_parts_per_chunk.load(); }
 
 uint64_t codag_kernel_launches(void) { return g_launches.load(); }
 

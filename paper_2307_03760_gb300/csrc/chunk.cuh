@@ -1,68 +1,250 @@
-// One chunk, end to end, for any format: bounds checks on the offsets
-// metadata (CODAG Sec. II-B: each chunk is located by its compressed and
-// uncompressed offsets), staging-ring start, the format decoder, and the
-// drain of in-flight staging copies.
+// One chunk (or one part of an RLE chunk), end to end, for any format:
+// bounds checks on the offsets metadata (CODAG Sec. II-B: each chunk is
+// located by its compressed and uncompressed offsets), staging-ring start,
+// the format decoder, and the drain of in-flight staging copies.
 #pragma once
 
 #include "kernels.cuh"
 
 namespace codag {
 
-// Decode (STORE) or size (!STORE) chunk c with the decoder of `family`.
-// Returns the chunk status; *produced = output bytes.
-template <int FAMILY, bool STORE, class Ring>
-__device__ __forceinline__ int32_t decode_chunk(Ring& ring, uint8_t* scratch, const Args& a,
-                                                uint64_t c, int format, uint64_t* produced) {
-  *produced = 0;
-  const uint64_t total = a.comp_off[a.n];
-  const uint64_t cs = a.comp_off[c], ce = a.comp_off[c + 1];
-  if (ce < cs || ce > total) return ST_BAD_SPAN;
-  uint64_t os = 0, cap = ~0ull;
-  if (STORE) {
-    os = a.out_off[c];
-    const uint64_t oe = a.out_off[c + 1];
-    if (oe < os) return ST_BAD_SPAN;
-    cap = oe - os;
-    if (FAMILY != 3 && ((cap & 7) || (os & 7))) return ST_BAD_SPAN;
-  }
-  const int64_t n_in = (int64_t)(ce - cs);
-  ring.start(a.comp + cs, n_in, a.comp + total);
-  int32_t st;
-  uint64_t prod = 0;
-  if (FAMILY == 1) {
-    const bool sgn = format == FMT_RLE_V1_I64;
-    st = rle_v1_decode<STORE>(ring, reinterpret_cast<uint16_t*>(scratch), n_in, sgn,
-                              reinterpret_cast<uint64_t*>(a.out + os), cap / 8, &prod);
-    prod *= 8;
-  } else if (FAMILY == 2) {
-    const bool sgn = format == FMT_RLE_V2_I64;
-    st = rle_v2_decode<STORE>(ring, scratch, n_in, sgn, reinterpret_cast<uint64_t*>(a.out + os),
-                              cap / 8, &prod);
-    prod *= 8;
-  } else {
-    st = inflate_decode<STORE, kLitTB, kDistTB, kWin>(ring, scratch, n_in, a.out + os, cap, &prod);
-  }
-  // bounded wait for this warp's own copies still in flight, also after a timeout
-  if (!ring.drain()) st = ST_TIMEOUT;
-  *produced = prod;
-  return st;
+// Combinable status: the earliest error in stream order wins; a timeout wins
+// over everything; ~0 means OK.
+__device__ __forceinline__ unsigned long long status_key(const PartResult& r) {
+  if (r.status == ST_OK) return ~0ull;
+  if (r.status == ST_TIMEOUT) return (unsigned long long)ST_TIMEOUT;
+  return ((unsigned long long)(r.err_pos + 1) << 4) | (unsigned long long)r.status;
+}
+__device__ __forceinline__ int32_t key_status(unsigned long long k) {
+  return k == ~0ull ? ST_OK : (int32_t)(k & 15);
 }
 
-// Body of the plain kernels: one warp per chunk, one chunk per warp.
-template <int FAMILY, bool STORE, int PER_WARP, class Ring>
-__device__ __forceinline__ void chunk_body(const Args& a) {
+// Offsets checks for chunk c: its compressed range and (STORE) output span.
+struct ChunkGeom {
+  int32_t bad;  // ST_OK or ST_BAD_SPAN
+  uint64_t cs;  // compressed start
+  int64_t n_in; // compressed bytes
+  uint64_t os;  // output start (STORE)
+  uint64_t cap; // output span (STORE; ~0 when sizing)
+};
+
+template <int FAMILY, bool STORE>
+__device__ __forceinline__ ChunkGeom chunk_geom(const Args& a, uint64_t c) {
+  ChunkGeom g{ST_OK, 0, 0, 0, ~0ull};
+  const uint64_t total = a.comp_off[a.n];
+  const uint64_t cs = a.comp_off[c], ce = a.comp_off[c + 1];
+  if (ce < cs || ce > total) { g.bad = ST_BAD_SPAN; return g; }
+  g.cs = cs;
+  g.n_in = (int64_t)(ce - cs);
+  if (STORE) {
+    g.os = a.out_off[c];
+    const uint64_t oe = a.out_off[c + 1];
+    if (oe < g.os) { g.bad = ST_BAD_SPAN; return g; }
+    g.cap = oe - g.os;
+    if (FAMILY != 3 && ((g.cap & 7) || (g.os & 7))) g.bad = ST_BAD_SPAN;
+  }
+  return g;
+}
+
+// Value index where part k of K starts (parts split the output evenly).
+__device__ __forceinline__ uint64_t part_target(uint64_t cap_v, uint32_t k, uint32_t K) {
+  if (k >= K) return ~0ull;
+  const uint64_t q = cap_v / K, rem = cap_v % K;
+  return q * k + (k < rem ? k : rem);
+}
+
+// Decode one part: the sub-stream of `in` starting at byte `base` (a run or
+// group boundary whose first value index is count0), through the runs that
+// start before value hi.  Error positions come back chunk-relative.
+template <int FAMILY, bool STORE, class In>
+__device__ __forceinline__ PartResult decode_rle_part(In& in, uint8_t* scratch, const Args& a,
+                                                      const ChunkGeom& g, int format, int64_t base,
+                                                      uint64_t count0, uint64_t hi) {
+  OffsetIn<In> sub{&in, base};
+  uint64_t* out = reinterpret_cast<uint64_t*>(a.out + g.os);
+  const uint64_t cap_v = g.cap / 8;
+  PartResult r;
+  if (FAMILY == 1)
+    r = rle_v1_part<STORE>(sub, reinterpret_cast<uint16_t*>(scratch), g.n_in - base,
+                           format == FMT_RLE_V1_I64, out, cap_v, count0, hi);
+  else
+    r = rle_v2_part<STORE>(sub, scratch, g.n_in - base, format == FMT_RLE_V2_I64, out, cap_v,
+                           count0, hi);
+  if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
+  r.count *= 8;
+  return r;
+}
+
+// Walk a chunk (one warp) to the start of part k: returns (position, count).
+template <int FAMILY, class In>
+__device__ __forceinline__ void walk_to(In& in, uint8_t* scratch, int64_t n_in, uint64_t target,
+                                        int64_t* pos, uint64_t* count) {
+  uint64_t t[2] = {0, target};
+  int64_t sp[2];
+  uint64_t sc[2];
+  if (FAMILY == 1)
+    rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), n_in, t, 1, sp, sc);
+  else
+    rle_v2_walk(in, n_in, t, 1, sp, sc);
+  // every lane computed the same values; lane 0 stored them
+  *pos = (int64_t)shfl64((uint64_t)sp[1], 0);
+  *count = shfl64(sc[1], 0);
+}
+
+// Part k of K of chunk c through a per-warp staging ring (batch kernel): the
+// warp walks to its start, then decodes its runs from there.
+template <int FAMILY, bool STORE, class Ring>
+__device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, const Args& a,
+                                                  uint64_t c, int format, uint32_t k, uint32_t K) {
+  const ChunkGeom g = chunk_geom<FAMILY, STORE>(a, c);
+  if (g.bad != ST_OK) return PartResult{g.bad, 0, 0};
+  ring.start(a.comp + g.cs, g.n_in, a.comp + a.comp_off[a.n]);
+  PartResult r;
+  if (FAMILY == 3) {
+    uint64_t prod = 0;
+    const int32_t st =
+        inflate_decode<STORE, kLitTB, kDistTB, kWin>(ring, scratch, g.n_in, a.out + g.os, g.cap, &prod);
+    r = PartResult{st, 0, prod};
+  } else {
+    const uint64_t cap_v = g.cap / 8;
+    int64_t base = 0;
+    uint64_t count0 = 0;
+    if (k > 0) walk_to<FAMILY>(ring, scratch, g.n_in, part_target(cap_v, k, K), &base, &count0);
+    const uint64_t hi = (k + 1 < K) ? part_target(cap_v, k + 1, K) : ~0ull;
+    r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, g, format, base, count0, hi);
+  }
+  // bounded wait for this warp's own copies still in flight, also after a timeout
+  if (!ring.drain()) r.status = ST_TIMEOUT;
+  return r;
+}
+
+// Plain RLE kernels: one CTA per chunk; its K warps decode the K parts and
+// combine their statuses in shared memory.  Shared memory: [stage][K scratch]
+// [mbarrier][key][split table].  A chunk that fits the stage is copied in
+// whole by TMA (issued by warp 0, one mbarrier); warp 0 walks it once to find
+// where the parts start, then every part decodes its runs in place.  A larger
+// chunk is streamed: warp 0 walks it through a ring, then each part streams
+// its own sub-stream through a ring of its own carved from the stage area.
+template <int FAMILY, bool STORE>
+__device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t K = blockDim.x >> 5;
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint64_t c = blockIdx.x;
+  uint8_t* stage = smem;
+  uint8_t* scratch = smem + stage_bytes + warp * kRleScratch;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + K * kRleScratch);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(bar + 1);
+  int64_t* split_pos = reinterpret_cast<int64_t*>(bar + 2);  // [17]
+  uint64_t* split_cnt = reinterpret_cast<uint64_t*>(split_pos + 17);  // [17]
+  uint64_t* target = split_cnt + 17;  // [17]
+  const ChunkGeom g = chunk_geom<FAMILY, STORE>(a, c);
+  if (g.bad != ST_OK) {
+    if (threadIdx.x == 0) {
+      a.status[c] = g.bad;
+      if (!STORE) a.sizes[c] = 0;
+    }
+    return;
+  }
+  const uint8_t* chunk = a.comp + g.cs;
+  const uint8_t* buf_end = a.comp + a.comp_off[a.n];
+  const uint8_t* gsrc = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(chunk) & ~uintptr_t(15));
+  const int64_t skew = chunk - gsrc;
+  const bool staged = staged_bytes(g.n_in) <= stage_bytes;
+  const uint64_t cap_v = g.cap / 8;
+  if (threadIdx.x == 0) {
+    *key = ~0ull;
+    split_pos[0] = 0;
+    split_cnt[0] = 0;
+    if (staged) {
+      mbar_init(bar, 1);
+      fence_mbar_init();
+      fence_proxy_async_smem();
+    }
+  }
+  if (threadIdx.x < K) target[threadIdx.x] = part_target(cap_v, threadIdx.x, K);
+  __syncthreads();
+  PartResult r;
+  if (staged) {
+    // readable: [gsrc, buf_end); copy up to the chunk end rounded to 16
+    int64_t bytes = (skew + g.n_in + 15) & ~int64_t(15);
+    if (bytes > buf_end - gsrc) bytes = buf_end - gsrc;
+    const uint32_t bulk = (uint32_t)bytes & ~15u;
+    const uint32_t tail = (uint32_t)bytes - bulk;
+    if (warp == 0) {
+      if (lane_id() == 0) {
+        mbar_arrive_expect_tx(bar, bulk);
+        for (uint32_t off = 0; off < bulk; off += 16384) {
+          const uint32_t piece = bulk - off < 16384 ? bulk - off : 16384;
+          tma_load_1d(stage + off, gsrc + off, piece, bar);
+        }
+      }
+      if (lane_id() < tail) stage[bulk + lane_id()] = __ldg(gsrc + bulk + lane_id());
+    }
+    bool ok = mbar_wait_bounded(bar, 0);
+    if (!ok) ok = mbar_wait_bounded(bar, 0);  // second bounded wait for the copies in flight
+    __syncthreads();  // also publishes warp 0's tail bytes
+    StagedInput in{stage, gsrc, skew};
+    if (ok && warp == 0 && K > 1) {
+      if (FAMILY == 1)
+        rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
+                    split_pos, split_cnt);
+      else
+        rle_v2_walk(in, g.n_in, target, (int)K - 1, split_pos, split_cnt);
+    }
+    __syncthreads();
+    if (!ok) {
+      r = PartResult{ST_TIMEOUT, 0, 0};
+    } else {
+      const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
+      r = decode_rle_part<FAMILY, STORE>(in, scratch, a, g, a.format, split_pos[warp],
+                                         split_cnt[warp], hi);
+    }
+  } else {
+    RleRing ring;
+    ring.init(stage + warp * RleRing::SMEM);
+    bool ok = true;
+    if (warp == 0 && K > 1) {
+      ring.start(chunk, g.n_in, buf_end);
+      if (FAMILY == 1)
+        rle_v1_walk(ring, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
+                    split_pos, split_cnt);
+      else
+        rle_v2_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
+      ok = ring.drain();
+    }
+    __syncthreads();
+    // this part's sub-stream, through a ring started at its first byte
+    const int64_t base = split_pos[warp];
+    ChunkGeom sub = g;
+    sub.n_in = g.n_in - base;
+    ring.start(chunk + base, sub.n_in, buf_end);
+    const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
+    r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, sub, a.format, 0, split_cnt[warp], hi);
+    if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
+    if (!ring.drain() || !ok) r.status = ST_TIMEOUT;
+  }
+  if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
+  __syncthreads();
+  if (threadIdx.x == 0) a.status[c] = key_status(*key);
+  if (!STORE && warp == K - 1 && lane_id() == 0) a.sizes[c] = r.count;
+}
+
+// Plain Deflate kernel: one warp per chunk.
+template <bool STORE>
+__device__ __forceinline__ void inflate_warp_body(const Args& a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint64_t c = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (c >= a.n) return;
-  uint8_t* region = smem + warp * PER_WARP;
-  Ring ring;
+  uint8_t* region = smem + warp * kDeflateWarp;
+  DeflateRing ring;
   ring.init(region);
-  uint64_t produced;
-  const int32_t st = decode_chunk<FAMILY, STORE>(ring, region + Ring::SMEM, a, c, a.format, &produced);
+  const PartResult r =
+      decode_part<3, STORE>(ring, region + DeflateRing::SMEM, a, c, FMT_DEFLATE, 0, 1);
   if (lane_id() == 0) {
-    a.status[c] = st;
-    if (!STORE) a.sizes[c] = produced;
+    a.status[c] = r.status;
+    if (!STORE) a.sizes[c] = r.count;
   }
 }
 

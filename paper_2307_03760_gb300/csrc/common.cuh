@@ -38,6 +38,20 @@ enum Format : int {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Result of decoding one part of a chunk: status, the stream position of the
+// run or group where it was found (errors of several parts are combined by
+// taking the earliest position, which is the first error in stream order),
+// and the values walked.
+struct PartResult {
+  int32_t status;
+  int64_t err_pos;
+  uint64_t count;
+};
+
+__device__ __forceinline__ PartResult part_error(int32_t st, int64_t pos, uint64_t count) {
+  return PartResult{st, pos, count};
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -51,6 +65,8 @@ __device__ __forceinline__ uint64_t bswap64(uint64_t x) {
   uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
   return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
 }
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
 
 // low `n` bits set, 0 <= n <= 64
 __device__ __forceinline__ uint64_t lowmask64(uint32_t n) {
@@ -67,6 +83,17 @@ __device__ __forceinline__ uint64_t shfl_up64(uint64_t v, int d) {
   uint32_t lo = __shfl_up_sync(FULL, (uint32_t)v, d);
   uint32_t hi = __shfl_up_sync(FULL, (uint32_t)(v >> 32), d);
   return ((uint64_t)hi << 32) | lo;
+}
+
+// inclusive prefix sum (mod 2^32) across the warp
+__device__ __forceinline__ uint32_t warp_incl_scan32(uint32_t v) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t t = __shfl_up_sync(FULL, v, d);
+    if (lane >= (uint32_t)d) v += t;
+  }
+  return v;
 }
 
 // inclusive prefix sum (mod 2^64) across the warp
@@ -117,14 +144,16 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       : "memory");
 }
 
+// Test a phase; the thread may be suspended (up to about 0.1 ms, the time
+// hint) until the phase completes, so waiting costs few instructions.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }

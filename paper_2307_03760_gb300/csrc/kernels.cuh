@@ -31,6 +31,14 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kRleV1Warp = round128(RleRing::SMEM + kRleV1Scratch);
 constexpr int kRleV2Warp = round128(RleRing::SMEM + kRleV2Scratch);
 constexpr int kDeflateWarp = round128(DeflateRing::SMEM + DeflateSmem::BYTES);
+// per-warp scratch of the RLE decoders besides their input
+constexpr int kRleScratch = 512;
+// plain RLE kernels: whole-chunk staging area per CTA (chunks up to about
+// 32 KiB compressed are staged in one piece) and the largest launch
+constexpr int kRleStageBytes = 32768 + 256;
+// per-CTA extras: mbarrier, status key, split positions/counts/targets
+constexpr int kRleCtaExtra = 16 + 3 * 17 * 8;
+constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra;
 constexpr int kBatchWarp =
     round128(RleRing::SMEM + cmax(DeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
 
@@ -44,11 +52,41 @@ struct Args {
   int32_t* status;      // per chunk
   int format;           // plain kernels: the format of every chunk
   const uint8_t* formats;  // batch kernel: per-chunk format
-  const uint32_t* order;   // batch kernel: claim order (may be null)
-  uint32_t* counter;       // batch kernel: work counter (zeroed before launch)
+  const uint32_t* order;   // batch kernel: chunks in claim order
+  uint32_t* counter;       // batch kernel: kBatchCounterWords words, zeroed before launch
+  unsigned long long* keys;  // batch kernel: combined status of multi-part chunks
+  int stage_bytes;           // plain RLE kernels: shared staging area per CTA
 };
 
-// Plain kernels (one warp per chunk) and sizing kernels, per format family.
+// Batch scratch: [0] task counter, [1..128] bucket histogram, [129..256]
+// bucket cursors.  Buckets order chunks largest first (2 * (63 - log2 of
+// compressed + uncompressed bytes) + 1 for Deflate); an RLE chunk of 2^b
+// bytes is split into clamp(2^(b-16), 1, 16) parts.
+constexpr int kBuckets = 128;
+constexpr int kBatchCounterWords = 1 + 2 * kBuckets;
+
+__host__ __device__ __forceinline__ bool is_rle_format(int f) {
+  return f == FMT_RLE_V1_I64 || f == FMT_RLE_V1_U64 || f == FMT_RLE_V2_I64 || f == FMT_RLE_V2_U64;
+}
+
+__device__ __forceinline__ uint32_t batch_bucket(const uint8_t* formats, const uint64_t* comp_off,
+                                                 const uint64_t* out_off, uint64_t c) {
+  const uint64_t b = (comp_off[c + 1] - comp_off[c]) + (out_off[c + 1] - out_off[c]);
+  const uint32_t lg = 63u - (uint32_t)__clzll((long long)(b | 1));
+  return 2u * (63u - lg) + (is_rle_format(formats[c]) ? 0u : 1u);
+}
+
+__host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
+  if (bucket & 1u) return 1u;
+  const int lg = 63 - (int)(bucket >> 1);
+  if (lg <= 16) return 1u;
+  return lg >= 20 ? 16u : (1u << (lg - 16));
+}
+
+// Plain kernels.  RLE: one CTA per chunk, blockDim.x / 32 warps decoding its
+// parts, dynamic shared memory = warps * per-warp size + 16.  Deflate: one
+// warp per chunk, kWarpsPerBlock warps per CTA.  *_sizes_* decode without
+// storing and write each chunk's decoded size (RLE: one warp per CTA).
 __global__ void rle_v1_kernel(Args a);
 __global__ void rle_v1_sizes_kernel(Args a);
 __global__ void rle_v2_kernel(Args a);
@@ -56,14 +94,21 @@ __global__ void rle_v2_sizes_kernel(Args a);
 __global__ void inflate_kernel(Args a);
 __global__ void inflate_sizes_kernel(Args a);
 
+// Persistent batch kernel: warps claim (chunk, part) tasks in bucket order.
 __global__ void batch_kernel(Args a);
 
-// descending-size claim order for the batch kernel (counting sort by
-// log2(compressed + uncompressed bytes)); hist/cursor are 64 words each
-__global__ void order_hist_kernel(const uint64_t* comp_off, const uint64_t* out_off, uint64_t n,
-                                  uint32_t* hist);
-__global__ void order_scatter_kernel(const uint64_t* comp_off, const uint64_t* out_off,
-                                     uint64_t n, const uint32_t* hist, uint32_t* cursor,
-                                     uint32_t* order);
+// claim order for the batch kernel (counting sort by bucket)
+__global__ void order_hist_kernel(const uint8_t* formats, const uint64_t* comp_off,
+                                  const uint64_t* out_off, uint64_t n, uint32_t* hist);
+__global__ void order_scatter_kernel(const uint8_t* formats, const uint64_t* comp_off,
+                                     const uint64_t* out_off, uint64_t n, const uint32_t* hist,
+                                     uint32_t* cursor, uint32_t* order);
+// status of multi-part chunks from their combined keys
+__global__ void batch_finalize_kernel(const uint8_t* formats, const uint64_t* comp_off,
+                                      const uint64_t* out_off, uint64_t n,
+                                      const unsigned long long* keys, int32_t* status);
+
+// Dynamic shared memory of the batch kernel: per-warp regions + bucket tables.
+constexpr int kBatchSmem = kWarpsPerBlock * kBatchWarp + 2 * (kBuckets + 1) * 4;
 
 }  // namespace codag

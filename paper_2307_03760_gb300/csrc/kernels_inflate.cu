@@ -3,11 +3,9 @@
 
 namespace codag {
 
-__global__ void __launch_bounds__(kThreads) inflate_kernel(Args a) {
-  chunk_body<3, true, kDeflateWarp, DeflateRing>(a);
-}
+__global__ void __launch_bounds__(kThreads) inflate_kernel(Args a) { inflate_warp_body<true>(a); }
 __global__ void __launch_bounds__(kThreads) inflate_sizes_kernel(Args a) {
-  chunk_body<3, false, kDeflateWarp, DeflateRing>(a);
+  inflate_warp_body<false>(a);
 }
 
 }  // namespace codag

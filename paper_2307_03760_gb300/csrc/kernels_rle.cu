@@ -1,19 +1,16 @@
-// Plain and sizing kernels for ORC RLE v1 and v2: one warp per chunk.
+// Plain and sizing kernels for ORC RLE v1 and v2: one CTA per chunk, one
+// part of the chunk per warp.
 #include "chunk.cuh"
 
 namespace codag {
 
-__global__ void __launch_bounds__(kThreads) rle_v1_kernel(Args a) {
-  chunk_body<1, true, kRleV1Warp, RleRing>(a);
+__global__ void __launch_bounds__(512) rle_v1_kernel(Args a) { rle_cta_body<1, true>(a, a.stage_bytes); }
+__global__ void __launch_bounds__(512) rle_v1_sizes_kernel(Args a) {
+  rle_cta_body<1, false>(a, a.stage_bytes);
 }
-__global__ void __launch_bounds__(kThreads) rle_v1_sizes_kernel(Args a) {
-  chunk_body<1, false, kRleV1Warp, RleRing>(a);
-}
-__global__ void __launch_bounds__(kThreads) rle_v2_kernel(Args a) {
-  chunk_body<2, true, kRleV2Warp, RleRing>(a);
-}
-__global__ void __launch_bounds__(kThreads) rle_v2_sizes_kernel(Args a) {
-  chunk_body<2, false, kRleV2Warp, RleRing>(a);
+__global__ void __launch_bounds__(512) rle_v2_kernel(Args a) { rle_cta_body<2, true>(a, a.stage_bytes); }
+__global__ void __launch_bounds__(512) rle_v2_sizes_kernel(Args a) {
+  rle_cta_body<2, false>(a, a.stage_bytes);
 }
 
 }  // namespace codag

@@ -8,18 +8,19 @@
 // whole device, is not acceptable.
 //
 // How: the batch kernel's scratch (claim counter, size histogram, claim
-// order) lives in the file-scope array below instead of the library
-// workspace.  The array is part of the library image, so every GPU that loads
-// the library holds it (about 257 KiB) until the process exits.  Host code
-// may not use the array's name as a device address; the first call on each
-// device, with that device current, asks the runtime for the array's address
-// with cudaGetSymbolAddress and keeps it.  That first call also sets the
-// kernel's shared-memory attribute, so make it before any stream capture.
+// order, combined status of split chunks) lives in the file-scope array
+// below instead of the library workspace.  The array is part of the library
+// image, so every GPU that loads the library holds it (about 385 KiB) until
+// the process exits.  Host code may not use the array's name as a device
+// address; the first call on each device, with that device current, asks the
+// runtime for the array's address with cudaGetSymbolAddress and keeps it.
+// That first call also sets the kernel's shared-memory attribute, so make it
+// before any stream capture.
 //
 // All calls on a device share the one array and it keeps the last call's
-// contents: each call clears the parts that must start at zero before its
-// kernels run.  Calls whose work overlaps on the GPU (for example on two
-// streams) race on the array and must not be issued.
+// contents: each call clears the parts that must start at zero (or all ones)
+// before its kernels run.  Calls whose work overlaps on the GPU (for example
+// on two streams) race on the array and must not be issued.
 #include <mutex>
 #include <string>
 
@@ -36,13 +37,17 @@ using namespace codag;
 namespace {
 
 constexpr uint64_t kMaxChunks = CODAG_NOALLOC_MAX_CHUNKS;
-constexpr int kCounterWords = 129;  // [0] claim counter, [1..64] histogram, [65..128] cursors
+// byte layout: combined status keys (u64 per chunk), counters, claim order
+constexpr size_t kKeysOff = 0;
+constexpr size_t kCountersOff = kKeysOff + kMaxChunks * 8;
+constexpr size_t kOrderOff = kCountersOff + ((kBatchCounterWords * 4 + 255) & ~size_t(255));
+constexpr size_t kScratchBytes = kOrderOff + kMaxChunks * 4;
 
-static __device__ __align__(256) uint32_t g_noalloc_scratch[kCounterWords + kMaxChunks];
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
 struct DeviceSetup {
   bool ready = false;
-  uint32_t* scratch = nullptr;  // device address of g_noalloc_scratch
+  uint8_t* scratch = nullptr;  // device address of g_noalloc_scratch
   int sm_count = 0;
   int fit = 0;  // resident batch CTAs per SM
 };
@@ -69,7 +74,7 @@ codag_status setup_current_device(DeviceSetup** out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess)
       return fail(CODAG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    const size_t smem = (size_t)kWarpsPerBlock * kBatchWarp;
+    const size_t smem = kBatchSmem;
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
       return fail(CODAG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -79,7 +84,7 @@ codag_status setup_current_device(DeviceSetup** out) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.fit, batch_kernel, kThreads, smem);
     if (e != cudaSuccess)
       return fail(CODAG_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
-    s.scratch = static_cast<uint32_t*>(p);
+    s.scratch = static_cast<uint8_t*>(p);
     s.ready = true;
   }
   *out = &s;
@@ -105,16 +110,18 @@ extern "C" codag_status codag_decompress_batch_noalloc(const uint8_t* formats, c
   DeviceSetup* s;
   codag_status st = setup_current_device(&s);
   if (st != CODAG_OK) return st;
-  uint32_t* counters = s->scratch;
-  uint32_t* order = s->scratch + kCounterWords;
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(s->scratch + kKeysOff);
+  uint32_t* counters = reinterpret_cast<uint32_t*>(s->scratch + kCountersOff);
+  uint32_t* order = reinterpret_cast<uint32_t*>(s->scratch + kOrderOff);
 
-  // the counter, histogram and cursors must start at zero on every call
-  cudaError_t e = cudaMemsetAsync(counters, 0, kCounterWords * sizeof(uint32_t), stream);
+  // the counter, histogram and cursors start at zero, the keys at all ones
+  cudaError_t e = cudaMemsetAsync(counters, 0, kBatchCounterWords * sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0xff, n_chunks * 8, stream);
   if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   const unsigned og = (unsigned)((n_chunks + 255) / 256 < 1024 ? (n_chunks + 255) / 256 : 1024);
-  order_hist_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n_chunks, counters + 1);
-  order_scatter_kernel<<<og, 256, 0, stream>>>(comp_offsets, out_offsets, n_chunks, counters + 1,
-                                               counters + 65, order);
+  order_hist_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n_chunks, counters + 1);
+  order_scatter_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n_chunks,
+                                               counters + 1, counters + 1 + kBuckets, order);
   Args a{};
   a.comp = static_cast<const uint8_t*>(comp);
   a.comp_off = comp_offsets;
@@ -125,15 +132,16 @@ extern "C" codag_status codag_decompress_batch_noalloc(const uint8_t* formats, c
   a.formats = formats;
   a.order = order;
   a.counter = counters;
+  a.keys = keys;
   int per_sm = codag_get_batch_ctas_per_sm();
   if (per_sm <= 0 || per_sm > s->fit) per_sm = s->fit;
   if (per_sm < 1) per_sm = 1;
-  uint64_t grid = (uint64_t)per_sm * (uint64_t)s->sm_count;
-  const uint64_t need = (n_chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (grid > need) grid = need;
-  batch_kernel<<<(unsigned)grid, kThreads, (size_t)kWarpsPerBlock * kBatchWarp, stream>>>(a);
+  const uint64_t grid = (uint64_t)per_sm * (uint64_t)s->sm_count;
+  batch_kernel<<<(unsigned)grid, kThreads, kBatchSmem, stream>>>(a);
+  batch_finalize_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n_chunks, keys,
+                                                chunk_status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
-  note_launches(3);
+  note_launches(4);
   return CODAG_OK;
 }

@@ -137,15 +137,72 @@ struct InRing {
   __device__ __forceinline__ uint8_t byte(int64_t p) const {
     return buf[(uint32_t)(p + skew) & (BYTES - 1)];
   }
+  // 4 bytes starting at p, little-endian (byte p in bits 0..7).  Only the low
+  // bits of p matter for the ring index, so 32-bit positions are enough.
+  __device__ __forceinline__ uint32_t u32(uint32_t p) const {
+    const uint32_t r = p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t lo = *reinterpret_cast<const uint32_t*>(buf + (a & (BYTES - 1)));
+    const uint32_t hi = *reinterpret_cast<const uint32_t*>(buf + ((a + 4) & (BYTES - 1)));
+    return __funnelshift_r(lo, hi, (r & 3u) * 8);
+  }
   // 8 bytes starting at p, little-endian (byte p in bits 0..7)
   __device__ __forceinline__ uint64_t u64(int64_t p) const {
-    const uint32_t r = (uint32_t)(p + skew);
-    const uint32_t a = r & ~7u;
-    const uint32_t sh = (r & 7u) * 8;
-    const uint64_t lo = *reinterpret_cast<const uint64_t*>(buf + (a & (BYTES - 1)));
-    const uint64_t hi = *reinterpret_cast<const uint64_t*>(buf + ((a + 8) & (BYTES - 1)));
-    return (lo >> sh) | ((hi << 1) << (63 - sh));
+    const uint32_t r = (uint32_t)p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sh = (r & 3u) * 8;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + (a & (BYTES - 1)));
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + ((a + 4) & (BYTES - 1)));
+    const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + ((a + 8) & (BYTES - 1)));
+    return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
   }
 };
+
+// Input that is wholly resident in shared memory: a CTA stages a whole
+// compressed chunk at once (TMA bulk copies on one mbarrier) and its warps
+// read it with the same interface as the ring, without further waits.
+struct StagedInput {
+  const uint8_t* buf;   // shared; position 0 = gsrc
+  const uint8_t* gsrc;  // 16-byte aligned global address of position 0
+  int64_t skew;         // chunk start - gsrc
+
+  __device__ __forceinline__ bool ensure(int64_t, int64_t) { return true; }
+  __device__ __forceinline__ bool drain() { return true; }
+  __device__ __forceinline__ const uint8_t* chunk_ptr() const { return gsrc + skew; }
+  __device__ __forceinline__ uint8_t byte(int64_t p) const { return buf[(uint32_t)(p + skew)]; }
+  __device__ __forceinline__ uint32_t u32(uint32_t p) const {
+    const uint32_t r = p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t lo = *reinterpret_cast<const uint32_t*>(buf + a);
+    const uint32_t hi = *reinterpret_cast<const uint32_t*>(buf + a + 4);
+    return __funnelshift_r(lo, hi, (r & 3u) * 8);
+  }
+  __device__ __forceinline__ uint64_t u64(int64_t p) const {
+    const uint32_t r = (uint32_t)p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sh = (r & 3u) * 8;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + a);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + a + 4);
+    const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + a + 8);
+    return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
+  }
+};
+
+// View of an input shifted by `base` bytes: a part decoder reads its own
+// sub-stream (starting at a run boundary) with positions from 0.
+template <class In>
+struct OffsetIn {
+  In* in;
+  int64_t base;
+  __device__ __forceinline__ bool ensure(int64_t lo, int64_t hi) { return in->ensure(lo + base, hi + base); }
+  __device__ __forceinline__ const uint8_t* chunk_ptr() const { return in->chunk_ptr() + base; }
+  __device__ __forceinline__ uint8_t byte(int64_t p) const { return in->byte(p + base); }
+  __device__ __forceinline__ uint32_t u32(uint32_t p) const { return in->u32(p + (uint32_t)base); }
+  __device__ __forceinline__ uint64_t u64(int64_t p) const { return in->u64(p + base); }
+};
+
+// Bytes a staged chunk of n_in bytes needs: 16-byte alignment skew in front,
+// and reads of up to 16 bytes past the last position (stale but in bounds).
+__host__ __device__ __forceinline__ int64_t staged_bytes(int64_t n_in) { return n_in + 15 + 32; }
 
 }  // namespace codag

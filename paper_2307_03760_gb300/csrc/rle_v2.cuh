@@ -47,150 +47,239 @@ __device__ __forceinline__ uint64_t v2_unpack(const Ring& ring, int64_t sec, uin
   return (x << (bit & 7)) >> (64 - w);
 }
 
-template <bool STORE, class Ring>
-__device__ int32_t rle_v2_decode(Ring& ring, uint8_t* scratch, int64_t n_in, bool is_signed,
-                                 uint64_t* __restrict__ out, uint64_t cap_values,
-                                 uint64_t* produced) {
+// value at bit offset `bit` (width w <= 25) of a packed section at chunk
+// position sec: one unaligned 4-byte read, a byte swap and two 32-bit shifts
+template <class In>
+__device__ __forceinline__ uint32_t v2_unpack32(const In& in, uint32_t sec, uint32_t bit, int w) {
+  const uint32_t x = bswap32(in.u32(sec + (bit >> 3)));
+  return (x << (bit & 7)) >> (32 - w);
+}
+
+__device__ __forceinline__ uint64_t unzigzag32(uint32_t v) {
+  return (uint64_t)(int64_t)(int32_t)((v >> 1) ^ (0u - (v & 1u)));
+}
+
+// One run's header fields and byte extent (everything that the header alone
+// decides).  Returns ST_OK, ST_TRUNCATED or ST_BAD_HEADER.
+struct V2Run {
+  uint32_t enc, len;
+  int w;
+  int64_t sec, nbytes, end;    // data section, its size, end of the run
+  int bw, pw, pll, ew;         // PATCHED_BASE
+  int64_t psec, pbytes;
+  uint64_t basev, dz;          // DELTA base and zigzagged delta base
+  uint32_t b0;
+};
+
+template <class In>
+__device__ __forceinline__ int32_t v2_parse_run(const In& in, int64_t pos, int64_t n_in, V2Run& r) {
+  const uint64_t hdr = in.u64(pos);
+  const uint32_t b0 = (uint32_t)(hdr & 0xff);
+  r.b0 = b0;
+  r.enc = b0 >> 6;
+  if (r.enc == 0) {  // SHORT_REPEAT
+    const int nb = ((b0 >> 3) & 7) + 1;
+    r.len = (b0 & 7) + 3;
+    r.w = nb;
+    r.end = pos + 1 + nb;
+    return r.end > n_in ? ST_TRUNCATED : ST_OK;
+  }
+  if (pos + 2 > n_in) return ST_TRUNCATED;
+  const uint32_t b1 = (uint32_t)((hdr >> 8) & 0xff);
+  const int wcode = (b0 >> 1) & 31;
+  r.len = (((b0 & 1) << 8) | b1) + 1;
+  if (r.enc == 1) {  // DIRECT
+    r.w = v2_width(wcode);
+    r.sec = pos + 2;
+    r.nbytes = ((int64_t)r.len * r.w + 7) >> 3;
+    r.end = r.sec + r.nbytes;
+    return r.end > n_in ? ST_TRUNCATED : ST_OK;
+  }
+  if (r.enc == 2) {  // PATCHED_BASE
+    r.w = v2_width(wcode);
+    if (pos + 4 > n_in) return ST_TRUNCATED;
+    const uint32_t b2 = (uint32_t)((hdr >> 16) & 0xff);
+    const uint32_t b3 = (uint32_t)((hdr >> 24) & 0xff);
+    r.bw = (b2 >> 5) + 1;
+    r.pw = v2_width(b2 & 31);
+    const int pgw = (b3 >> 5) + 1;
+    r.pll = b3 & 31;
+    if (pgw + r.pw > 64) return ST_BAD_HEADER;
+    if (pos + 4 + r.bw > n_in) return ST_TRUNCATED;
+    r.sec = pos + 4 + r.bw;
+    r.nbytes = ((int64_t)r.len * r.w + 7) >> 3;
+    if (r.sec + r.nbytes > n_in) return ST_TRUNCATED;
+    r.ew = v2_closest_fixed_bits(pgw + r.pw);
+    r.psec = r.sec + r.nbytes;
+    r.pbytes = ((int64_t)r.pll * r.ew + 7) >> 3;
+    r.end = r.psec + r.pbytes;
+    return r.end > n_in ? ST_TRUNCATED : ST_OK;
+  }
+  // DELTA
+  r.w = wcode == 0 ? 0 : v2_width(wcode);
+  int l1, l2;
+  int32_t st = varint_at(in, pos + 2, n_in - (pos + 2), &r.basev, &l1);
+  if (st != ST_OK) return st;
+  st = varint_at(in, pos + 2 + l1, n_in - (pos + 2 + l1), &r.dz, &l2);
+  if (st != ST_OK) return st;
+  r.sec = pos + 2 + l1 + l2;
+  r.nbytes = (r.w != 0 && r.len >= 2) ? ((int64_t)(r.len - 2) * r.w + 7) >> 3 : 0;
+  r.end = r.sec + r.nbytes;
+  return r.end > n_in ? ST_TRUNCATED : ST_OK;
+}
+
+// Walk an RLE v2 stream's run headers (one warp, identical state in every
+// lane) and record where parts start: for k = 1..nsplit, the first run whose
+// first value index is >= target[k].  Where the walk stops early (a header
+// error, or the end of the stream) the remaining splits get that position,
+// so the last part finds the error again.  split_pos / split_cnt: shared.
+template <class In>
+__device__ __forceinline__ void rle_v2_walk(In& in, int64_t n_in, const uint64_t* target,
+                                            int nsplit, int64_t* split_pos, uint64_t* split_cnt) {
+  int64_t pos = 0;
+  uint64_t count = 0;
+  int k = 1;
+  while (pos < n_in && k <= nsplit) {
+    while (k <= nsplit && count >= target[k]) {
+      if (lane_id() == 0) {
+        split_pos[k] = pos;
+        split_cnt[k] = count;
+      }
+      k++;
+    }
+    if (k > nsplit) break;
+    if (!in.ensure(pos, pos + 40)) break;
+    V2Run r;
+    if (v2_parse_run(in, pos, n_in, r) != ST_OK) break;
+    count += r.len;
+    pos = r.end;
+  }
+  for (; k <= nsplit; k++)
+    if (lane_id() == 0) {
+      split_pos[k] = pos;
+      split_cnt[k] = count;
+    }
+}
+
+// Decode part of one RLE v2 chunk.  The part's stream starts at a run
+// boundary (position 0 of `in`, n_in bytes to the chunk end) whose first
+// value index is count0; it decodes every run that starts before value hi_v
+// (hi_v = ~0: to the end of the stream, and report OUTPUT_UNDERFLOW).
+// out: the chunk's output; cap_values: its span; STORE = false sizes only.
+// Error positions are relative to the part's start.
+template <bool STORE, class In>
+__device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool is_signed,
+                                  uint64_t* __restrict__ out, uint64_t cap_values, uint64_t count0,
+                                  uint64_t hi_v) {
   const uint32_t lane = lane_id();
   uint32_t* bitmap = reinterpret_cast<uint32_t*>(scratch);
   uint64_t* pvals = reinterpret_cast<uint64_t*>(scratch + 64);
+  const bool last = hi_v == ~0ull;
   int64_t pos = 0;
-  uint64_t count = 0;
-  *produced = 0;
+  uint64_t count = count0;
   while (pos < n_in) {
-    if (!ring.ensure(pos, pos + 40)) return ST_TIMEOUT;
-    const uint64_t hdr = ring.u64(pos);
-    const uint32_t b0 = (uint32_t)(hdr & 0xff);
-    const uint32_t enc = b0 >> 6;
-    if (enc == 0) {  // SHORT_REPEAT
-      const int nb = ((b0 >> 3) & 7) + 1;
-      const uint32_t len = (b0 & 7) + 3;
-      if (pos + 1 + nb > n_in) return ST_TRUNCATED;
-      uint64_t v = bswap64(ring.u64(pos + 1)) >> (64 - 8 * nb);
-      if (is_signed) v = unzigzag(v);
-      if (len > cap_values - count) return ST_OVERFLOW;
-      if (STORE && lane < len) out[count + lane] = v;
-      count += len;
-      pos += 1 + nb;
-    } else {
-      if (pos + 2 > n_in) return ST_TRUNCATED;
-      const uint32_t b1 = (uint32_t)((hdr >> 8) & 0xff);
-      const int wcode = (b0 >> 1) & 31;
-      const uint32_t len = (((b0 & 1) << 8) | b1) + 1;
-      if (enc == 1) {  // DIRECT
-        const int w = v2_width(wcode);
-        const int64_t sec = pos + 2;
-        const int64_t nbytes = ((int64_t)len * w + 7) >> 3;
-        if (sec + nbytes > n_in) return ST_TRUNCATED;
-        if (len > cap_values - count) return ST_OVERFLOW;
-        if (STORE) {
-          for (uint32_t i0 = 0; i0 < len; i0 += 32) {
-            const int64_t lo = sec + (((int64_t)i0 * w) >> 3);
-            if (!ring.ensure(lo, lo + 4 * w + 16)) return ST_TIMEOUT;
-            const uint32_t i = i0 + lane;
-            if (i < len) {
-              uint64_t v = v2_unpack(ring, sec, i, w);
-              if (is_signed) v = unzigzag(v);
-              out[count + i] = v;
-            }
-          }
-        }
-        count += len;
-        pos = sec + nbytes;
-      } else if (enc == 2) {  // PATCHED_BASE
-        const int w = v2_width(wcode);
-        if (pos + 4 > n_in) return ST_TRUNCATED;
-        const uint32_t b2 = (uint32_t)((hdr >> 16) & 0xff);
-        const uint32_t b3 = (uint32_t)((hdr >> 24) & 0xff);
-        const int bw = (b2 >> 5) + 1;
-        const int pw = v2_width(b2 & 31);
-        const int pgw = (b3 >> 5) + 1;
-        const int pll = b3 & 31;
-        if (pgw + pw > 64) return ST_BAD_HEADER;
-        if (pos + 4 + bw > n_in) return ST_TRUNCATED;
-        const uint64_t mag = bswap64(ring.u64(pos + 4)) >> (64 - 8 * bw);
-        const uint64_t sign = 1ull << (8 * bw - 1);
-        const uint64_t base = (mag & sign) ? 0ull - (mag & ~sign) : mag;
-        const int64_t sec = pos + 4 + bw;
-        const int64_t nbytes = ((int64_t)len * w + 7) >> 3;
-        if (sec + nbytes > n_in) return ST_TRUNCATED;
-        const int ew = v2_closest_fixed_bits(pgw + pw);
-        const int64_t psec = sec + nbytes;
-        const int64_t pbytes = ((int64_t)pll * ew + 7) >> 3;
-        if (psec + pbytes > n_in) return ST_TRUNCATED;
-        // patch list: one entry per lane, read straight from global memory
-        // (at most 31 entries) so the staging ring only ever moves forward;
-        // positions = prefix sum of the gaps
-        uint64_t gap = 0, patch = 0;
-        if ((int)lane < pll) {
-          const uint64_t bit = (uint64_t)lane * (uint64_t)ew;
-          const int64_t at = psec + (int64_t)(bit >> 3);
-          const uint8_t* src = ring.chunk_ptr();
-          uint64_t x = 0;
+    if (count >= hi_v) return PartResult{ST_OK, -1, count};
+    if (!in.ensure(pos, pos + 40)) return part_error(ST_TIMEOUT, 0, count);
+    V2Run r;
+    const int32_t st = v2_parse_run(in, pos, n_in, r);
+    if (st != ST_OK) return part_error(st, pos, count);
+    const uint32_t len = r.len;
+    const int w = r.w;
+    if (r.enc == 2) {  // patch list validity belongs to the run's own checks
+      const uint64_t mag = bswap64(in.u64(pos + 4)) >> (64 - 8 * r.bw);
+      const uint64_t sign = 1ull << (8 * r.bw - 1);
+      const uint64_t base = (mag & sign) ? 0ull - (mag & ~sign) : mag;
+      // one entry per lane, read straight from global memory (at most 31
+      // entries) so the staging ring only ever moves forward; positions are
+      // the prefix sum of the gaps
+      uint64_t gap = 0, patch = 0;
+      if ((int)lane < r.pll) {
+        const uint64_t bit = (uint64_t)lane * (uint64_t)r.ew;
+        const int64_t at = r.psec + (int64_t)(bit >> 3);
+        const uint8_t* src = in.chunk_ptr();
+        uint64_t x = 0;
 #pragma unroll
-          for (int k = 0; k < 8; k++) {
-            const uint64_t b = at + k < n_in ? (uint64_t)__ldg(src + at + k) : 0ull;
-            x = (x << 8) | b;
-          }
-          const uint64_t e = (x << (bit & 7)) >> (64 - ew);
-          gap = e >> pw;  // pw <= 63 here
-          patch = e & lowmask64(pw);
+        for (int k = 0; k < 8; k++) {
+          const uint64_t b = at + k < n_in ? (uint64_t)__ldg(src + at + k) : 0ull;
+          x = (x << 8) | b;
         }
-        const bool real = (int)lane < pll && !(gap == 255 && patch == 0);
-        const uint64_t ppos = warp_incl_scan64(gap);
-        const uint32_t real_mask = __ballot_sync(FULL, real);
-        const uint32_t before = real_mask & lanemask_lt();
-        const int prev = before ? 31 - __clz(before) : 0;
-        const uint64_t prev_pos = shfl64(ppos, prev);
-        const bool bad = real && (ppos >= len || (before != 0 && ppos <= prev_pos));
-        if (__ballot_sync(FULL, bad)) return ST_BAD_HEADER;
-        if (len > cap_values - count) return ST_OVERFLOW;
-        if (STORE) {
-          if (lane < 16) bitmap[lane] = 0;
-          __syncwarp();
-          if (real) {
-            atomicOr(&bitmap[ppos >> 5], 1u << (ppos & 31));
-            pvals[__popc(before)] = patch;
+        const uint64_t e = (x << (bit & 7)) >> (64 - r.ew);
+        gap = e >> r.pw;  // pw <= 63 here
+        patch = e & lowmask64(r.pw);
+      }
+      const bool real = (int)lane < r.pll && !(gap == 255 && patch == 0);
+      const uint64_t ppos = warp_incl_scan64(gap);
+      const uint32_t before = __ballot_sync(FULL, real) & lanemask_lt();
+      const int prev = before ? 31 - __clz(before) : 0;
+      const uint64_t prev_pos = shfl64(ppos, prev);
+      const bool bad = real && (ppos >= len || (before != 0 && ppos <= prev_pos));
+      if (__ballot_sync(FULL, bad)) return part_error(ST_BAD_HEADER, pos, count);
+      if (count > cap_values || len > cap_values - count) return part_error(ST_OVERFLOW, pos, count);
+      if (STORE) {
+        if (lane < 16) bitmap[lane] = 0;
+        __syncwarp();
+        if (real) {
+          atomicOr(&bitmap[ppos >> 5], 1u << (ppos & 31));
+          pvals[__popc(before)] = patch;
+        }
+        __syncwarp();
+        uint32_t carry = 0;
+        uint64_t* o = out + count;
+        const bool narrow = w <= 25;
+        if (narrow && !in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
+        for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+          if (!narrow) {
+            const int64_t lo = r.sec + (((int64_t)i0 * w) >> 3);
+            if (!in.ensure(lo, lo + 4 * w + 16)) return part_error(ST_TIMEOUT, 0, count);
           }
-          __syncwarp();
-          uint32_t carry = 0;
-          for (uint32_t i0 = 0; i0 < len; i0 += 32) {
-            const int64_t lo = sec + (((int64_t)i0 * w) >> 3);
-            if (!ring.ensure(lo, lo + 4 * w + 16)) return ST_TIMEOUT;
-            const uint32_t word = bitmap[i0 >> 5];
-            const uint32_t i = i0 + lane;
-            if (i < len) {
-              uint64_t v = v2_unpack(ring, sec, i, w);
-              if ((word >> lane) & 1u) {
-                const uint64_t pv = pvals[carry + __popc(word & lanemask_lt())];
-                if (w < 64) v |= pv << w;
-              }
-              out[count + i] = base + v;
+          const uint32_t word = bitmap[i0 >> 5];
+          const uint32_t i = i0 + lane;
+          if (i < len) {
+            uint64_t v = narrow ? (uint64_t)v2_unpack32(in, (uint32_t)r.sec, i * (uint32_t)w, w)
+                                : v2_unpack(in, r.sec, i, w);
+            if ((word >> lane) & 1u) {
+              const uint64_t pv = pvals[carry + __popc(word & lanemask_lt())];
+              if (w < 64) v |= pv << w;
             }
-            carry += __popc(word);
+            o[i] = base + v;
           }
+          carry += __popc(word);
         }
-        count += len;
-        pos = psec + pbytes;
-      } else {  // DELTA
-        const int w = wcode == 0 ? 0 : v2_width(wcode);
-        uint64_t basev, dz;
-        int l1, l2;
-        int32_t st = varint_at(ring, pos + 2, n_in - (pos + 2), &basev, &l1);
-        if (st != ST_OK) return st;
-        if (is_signed) basev = unzigzag(basev);
-        st = varint_at(ring, pos + 2 + l1, n_in - (pos + 2 + l1), &dz, &l2);
-        if (st != ST_OK) return st;
-        const uint64_t delta = unzigzag(dz);
-        const int64_t sec = pos + 2 + l1 + l2;
-        int64_t nbytes = 0;
-        if (w != 0 && len >= 2) {
-          nbytes = ((int64_t)(len - 2) * w + 7) >> 3;
-          if (sec + nbytes > n_in) return ST_TRUNCATED;
-        }
-        if (len > cap_values - count) return ST_OVERFLOW;
-        if (STORE) {
-          uint64_t* o = out + count;
+        __syncwarp();
+      }
+    } else {
+      if (count > cap_values || len > cap_values - count) return part_error(ST_OVERFLOW, pos, count);
+      if (STORE) {
+        uint64_t* o = out + count;
+        if (r.enc == 0) {  // SHORT_REPEAT
+          uint64_t v = bswap64(in.u64(pos + 1)) >> (64 - 8 * w);
+          if (is_signed) v = unzigzag(v);
+          if (lane < len) o[lane] = v;
+        } else if (r.enc == 1) {  // DIRECT
+          if (w <= 25) {  // whole run resident at once (<= 1600 bytes), 32-bit unpack
+            if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
+            const uint32_t sec32 = (uint32_t)r.sec;
+            uint32_t bit = lane * (uint32_t)w;
+            for (uint32_t i = lane; i < len; i += 32, bit += 32u * (uint32_t)w) {
+              const uint32_t v = v2_unpack32(in, sec32, bit, w);
+              o[i] = is_signed ? unzigzag32(v) : (uint64_t)v;
+            }
+          } else {
+            for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+              const int64_t lo = r.sec + (((int64_t)i0 * w) >> 3);
+              if (!in.ensure(lo, lo + 4 * w + 16)) return part_error(ST_TIMEOUT, 0, count);
+              const uint32_t i = i0 + lane;
+              if (i < len) {
+                uint64_t v = v2_unpack(in, r.sec, i, w);
+                if (is_signed) v = unzigzag(v);
+                o[i] = v;
+              }
+            }
+          }
+        } else {  // DELTA
+          uint64_t basev = r.basev;
+          if (is_signed) basev = unzigzag(basev);
+          const uint64_t delta = unzigzag(r.dz);
           if (w == 0 || len < 3) {
             for (uint32_t i = lane; i < len; i += 32) o[i] = basev + (uint64_t)i * delta;
           } else {
@@ -199,27 +288,39 @@ __device__ int32_t rle_v2_decode(Ring& ring, uint8_t* scratch, int64_t n_in, boo
             if (lane == 1) o[1] = basev + delta;
             uint64_t carry = basev + delta;
             const uint32_t nd = len - 2;
-            for (uint32_t j0 = 0; j0 < nd; j0 += 32) {
-              const int64_t lo = sec + (((int64_t)j0 * w) >> 3);
-              if (!ring.ensure(lo, lo + 4 * w + 16)) return ST_TIMEOUT;
-              const uint32_t j = j0 + lane;
-              uint64_t d = j < nd ? v2_unpack(ring, sec, j, w) : 0;
-              if (negative) d = 0ull - d;
-              const uint64_t s = warp_incl_scan64(d) + carry;
-              if (j < nd) o[2 + j] = s;
-              carry = shfl64(s, 31);
+            if (w <= 26) {  // 32 deltas of <= 26 bits sum below 2^31: 32-bit scan
+              if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
+              const uint32_t sec32 = (uint32_t)r.sec;
+              uint32_t bit = lane * (uint32_t)w;
+              for (uint32_t j0 = 0; j0 < nd; j0 += 32, bit += 32u * (uint32_t)w) {
+                const uint32_t j = j0 + lane;
+                const uint32_t d = j < nd ? v2_unpack32(in, sec32, bit, w) : 0u;
+                const uint32_t sc = warp_incl_scan32(d);
+                const uint64_t s = negative ? carry - (uint64_t)sc : carry + (uint64_t)sc;
+                if (j < nd) o[2 + j] = s;
+                carry = shfl64(s, 31);
+              }
+            } else {
+              for (uint32_t j0 = 0; j0 < nd; j0 += 32) {
+                const int64_t lo = r.sec + (((int64_t)j0 * w) >> 3);
+                if (!in.ensure(lo, lo + 4 * w + 16)) return part_error(ST_TIMEOUT, 0, count);
+                const uint32_t j = j0 + lane;
+                uint64_t d = j < nd ? v2_unpack(in, r.sec, j, w) : 0;
+                if (negative) d = 0ull - d;
+                const uint64_t s = warp_incl_scan64(d) + carry;
+                if (j < nd) o[2 + j] = s;
+                carry = shfl64(s, 31);
+              }
             }
           }
         }
-        count += len;
-        pos = sec + nbytes;
       }
     }
-    *produced = count;
+    count += len;
+    pos = r.end;
   }
-  *produced = count;
-  if (STORE && count < cap_values) return ST_UNDERFLOW;
-  return ST_OK;
+  if (last && STORE && count < cap_values) return part_error(ST_UNDERFLOW, n_in, count);
+  return PartResult{ST_OK, -1, count};
 }
 
 }  // namespace codag

@@ -53,8 +53,10 @@ def test_golden_fixtures(fmt):
 
 
 @pytest.mark.parametrize("fmt", ALL_FMTS)
-def test_workload_parity_small(fmt):
+def test_workload_parity_small(fmt, parts):
     """Several chunks per SM tile plus ragged chunk sizes."""
+    if fmt == 3 and parts:
+        pytest.skip("parts apply to RLE only")
     if fmt == 3:
         sizes = [65536] * 40 + [1, 7, 100, 4095, 4096, 4097, 70000, 131072]
     else:
@@ -121,9 +123,21 @@ def test_short_streams_exhaustive(fmt):
     assert (gsz[sst == 0] == sz[sst == 0]).all()
 
 
+@pytest.fixture(params=[0, 1, 16], ids=["parts_auto", "parts_1", "parts_16"])
+def parts(request):
+    """Plain RLE calls split every chunk into this many warp-decoded parts."""
+    import paper_2307_03760_gb300 as codag
+    codag.codag_set_parts_per_chunk(request.param)
+    yield request.param
+    codag.codag_set_parts_per_chunk(0)
+
+
 @pytest.mark.parametrize("fmt", ALL_FMTS)
-def test_mutated_streams(fmt):
-    """Bit flips, truncations and splices of valid chunks."""
+def test_mutated_streams(fmt, parts):
+    """Bit flips, truncations and splices of valid chunks; the chunk status
+    combined over parts must still be the first error in stream order."""
+    if fmt == 3 and parts:
+        pytest.skip("parts apply to RLE only")
     rng = random.Random(100 + fmt)
     base = synth.build_chunks([fmt] * 8, [4096 if fmt != 3 else 5000] * 8, seed=41)
     chunks = []
@@ -156,7 +170,9 @@ def test_mutated_streams(fmt):
 
 
 @pytest.mark.parametrize("fmt", [1, 2, 3])
-def test_every_prefix_of_a_chunk(fmt):
+def test_every_prefix_of_a_chunk(fmt, parts):
+    if fmt == 3 and parts:
+        pytest.skip("parts apply to RLE only")
     w = synth.build_chunks([fmt], [8 * 700 if fmt != 3 else 3000], seed=51)
     src = w.comp.tobytes()
     chunks = [src[:k] for k in range(len(src) + 1)]
@@ -186,7 +202,8 @@ def test_empty_chunks_and_offsets():
 
 
 def test_batch_mixed_and_graph():
-    w = synth.batched(seed=3, n_chunks=600, lo=512, hi=1 << 18, keep_plain=True)
+    """Includes chunks up to 1 MiB, which the batch kernel splits into parts."""
+    w = synth.batched(seed=3, n_chunks=600, lo=512, hi=1 << 20, keep_plain=True)
     got, st = run_batch(w.formats, w.comp, w.comp_off, w.out_off)
     assert (st == 0).all() and np.array_equal(got, w.plain)
     got2, st2 = run_batch(w.formats, w.comp, w.comp_off, w.out_off, graph=True, replays=3)
@@ -194,12 +211,15 @@ def test_batch_mixed_and_graph():
 
 
 def test_batch_unknown_format_and_errors():
-    w = synth.batched(seed=4, n_chunks=64, lo=512, hi=1 << 14)
+    w = synth.batched(seed=4, n_chunks=64, lo=512, hi=1 << 20)
     fm = w.formats.copy()
     fm[5] = 9
     comp = w.comp.copy()
-    a = int(w.comp_off[7])
-    comp[a] ^= 0xFF
+    rng = np.random.default_rng(7)
+    for c in range(6, w.n, 3):  # corrupt a byte in every third chunk, big ones included
+        a, b = int(w.comp_off[c]), int(w.comp_off[c + 1])
+        if b > a:
+            comp[rng.integers(a, b)] ^= 0x5A
     got, st = run_batch(fm, comp, w.comp_off, w.out_off)
     assert st[5] == oracle.BAD_HEADER
     fm2 = fm.copy()
