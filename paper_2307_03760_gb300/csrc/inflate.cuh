@@ -28,7 +28,8 @@
 
 namespace codag {
 
-// table entry: bits 0-3 code length, 4-6 kind, 8-11 extra bits, 16-31 value
+// table entry: bits 0-3 code length, 4-6 kind, 8-11 extra bits, 16-30 value,
+// bit 31 set for literals (so a literal is recognised by the sign alone)
 enum : uint32_t {
   K_LIT = 0,      // literal byte / code-length symbol
   K_BASE = 1,     // length or distance base with extra bits
@@ -41,10 +42,10 @@ enum : uint32_t {
 __device__ __forceinline__ uint32_t ent_len(uint32_t e) { return e & 15u; }
 __device__ __forceinline__ uint32_t ent_kind(uint32_t e) { return (e >> 4) & 7u; }
 __device__ __forceinline__ uint32_t ent_extra(uint32_t e) { return (e >> 8) & 15u; }
-__device__ __forceinline__ uint32_t ent_val(uint32_t e) { return e >> 16; }
+__device__ __forceinline__ uint32_t ent_val(uint32_t e) { return (e >> 16) & 0x7fffu; }
 __device__ __forceinline__ uint32_t make_ent(uint32_t len, uint32_t kind, uint32_t extra,
                                              uint32_t val) {
-  return len | (kind << 4) | (extra << 8) | (val << 16);
+  return len | (kind << 4) | (extra << 8) | (val << 16) | (kind == 0 ? 0x80000000u : 0u);
 }
 
 // RFC 1951 Sec. 3.2.5 in closed form: length symbol 257+i, distance code d.
@@ -197,7 +198,7 @@ struct InflateSmem {
   static constexpr int OFF_LIT = 0;
   static constexpr int OFF_DIST = OFF_LIT + 4 * LIT_ENTRIES;
   static constexpr int OFF_WIN = OFF_DIST + 4 * DIST_ENTRIES;
-  static constexpr int OFF_LSORT = OFF_WIN + WIN;
+  static constexpr int OFF_LSORT = OFF_WIN + WIN;  // WIN = 0: no shared window
   static constexpr int OFF_DSORT = OFF_LSORT + 2 * 288;
   static constexpr int OFF_META = OFF_DSORT + 2 * 32;  // 7 x u16[16]
   static constexpr int OFF_LENS = OFF_META + 7 * 32;
@@ -205,43 +206,66 @@ struct InflateSmem {
 };
 
 // Bit reader over the staging ring; all lanes hold the same state.
-template <class Ring>
+// bb holds nb valid stream bits (least significant = next); inpos is the
+// next byte not yet loaded.  Bits past the chunk end read as zero.
+template <class In>
 struct BitIn {
-  Ring* ring;
-  uint64_t bb;     // next bits, LSB first; zero past the chunk end
-  int nb;          // valid bits in bb
-  int64_t pos;     // absolute bit position of bb's bit 0
-  int64_t endbits; // chunk length in bits
+  In* in;
+  uint64_t bb;
+  uint32_t nb;
+  uint32_t inpos;
+  uint32_t n_in;
 
+  // Top up to >= 56 bits (or every remaining byte near the end).
   __device__ __forceinline__ bool refill() {
-    const int64_t byte = pos >> 3;
-    if (!ring->ensure(byte, byte + 8)) return false;
-    const uint32_t sh = (uint32_t)(pos & 7);
-    uint64_t x = ring->u64(byte) >> sh;
-    const int64_t avail = endbits - pos;
-    if (avail < 64) x &= lowmask64(avail < 0 ? 0u : (uint32_t)avail);
-    bb = x;
-    nb = 64 - (int)sh;
+    // keep 8 bytes behind inpos resident: a stored block starts up to 8
+    // bytes before the next unloaded byte
+    const uint32_t keep = inpos >= 8 ? inpos - 8 : 0;
+    if (inpos + 8 <= n_in) {  // branchless refill: 8 real bytes are there
+      if (!in->ensure(keep, inpos + 8)) return false;
+      bb |= in->u64(inpos) << nb;
+      inpos += (63 - nb) >> 3;
+      nb |= 56;
+      return true;
+    }
+    if (inpos < n_in && !in->ensure(keep, n_in)) return false;
+    while (nb <= 56 && inpos < n_in) {
+      bb |= (uint64_t)in->byte(inpos) << nb;
+      nb += 8;
+      inpos++;
+    }
     return true;
   }
+  __device__ __forceinline__ uint32_t avail() const { return nb + 8u * (n_in - inpos); }
   __device__ __forceinline__ void consume(uint32_t k) {
     bb >>= k;
-    nb -= (int)k;
-    pos += k;
+    nb -= k;
   }
-  __device__ __forceinline__ int64_t avail() const { return endbits - pos; }
+  // byte position of the next unconsumed bit (which must be byte aligned)
+  __device__ __forceinline__ uint32_t byte_pos() const { return inpos - (nb >> 3); }
+  __device__ __forceinline__ void seek_byte(uint32_t p) {
+    inpos = p;
+    bb = 0;
+    nb = 0;
+  }
 };
 
 // Decode one raw Deflate chunk.  out: the chunk's output; cap: its span in
-// bytes (STORE = false sizes the stream and ignores out/cap).
+// bytes (STORE = false sizes the stream and ignores out/cap).  Chunks must be
+// below 512 MiB compressed and 4 GiB decoded (32-bit positions).
 template <bool STORE, int LIT_TB, int DIST_TB, int WIN, class Ring>
-__device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in,
-                                  uint8_t* __restrict__ out, uint64_t cap, uint64_t* produced) {
+__device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
+                                  uint8_t* __restrict__ out, uint64_t cap64, uint64_t* produced) {
   using SM = InflateSmem<LIT_TB, DIST_TB, WIN>;
-  constexpr uint32_t WMASK = WIN - 1;
-  constexpr int64_t FLUSH_T = WIN / 4;
-  constexpr int64_t NEAR_MAX = WIN - 512;
-  static_assert(WIN >= 2048 && (WIN & (WIN - 1)) == 0, "window: power of two >= 2048");
+  constexpr uint32_t WMASK = WIN == 0 ? 0 : WIN - 1;
+  constexpr uint32_t FLUSH_T = WIN == 0 ? 0xffffffffu : WIN / 4;
+  constexpr uint32_t NEAR_MAX = WIN == 0 ? 0xffffffffu : WIN - 512;
+  constexpr uint32_t LITMASK = (1u << LIT_TB) - 1;
+  constexpr uint32_t DISTMASK = (1u << DIST_TB) - 1;
+  static_assert(WIN == 0 || (WIN >= 2048 && (WIN & (WIN - 1)) == 0), "window: 0 or a power of two >= 2048");
+  constexpr bool GWIN = WIN == 0;  // output and match sources in global memory
+  *produced = 0;
+  if (n_in64 >= (int64_t)1 << 29 || (STORE && cap64 > 0xffffffffull)) return ST_BAD_SPAN;
   const uint32_t lane = lane_id();
   uint32_t* lit_tab = reinterpret_cast<uint32_t*>(scratch + SM::OFF_LIT);
   uint32_t* dist_tab = reinterpret_cast<uint32_t*>(scratch + SM::OFF_DIST);
@@ -254,71 +278,108 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in,
              meta + 80, 0, DIST_TB, 2};
   uint16_t* run16 = meta + 96;
 
-  BitIn<Ring> in{&ring, 0, 0, 0, n_in * 8};
+  const uint32_t n_in = (uint32_t)n_in64;
+  BitIn<Ring> in{&ring, 0, 0, 0, n_in};
   const uint32_t oaddr = (uint32_t)reinterpret_cast<uintptr_t>(out);
-  const uint64_t limit = STORE ? cap : ~0ull;
-  uint64_t wpos = 0;     // bytes produced
-  uint64_t flushed = 0;  // bytes already in global memory
+  const uint32_t limit = STORE ? (uint32_t)cap64 : 0xffffffffu;
+  uint32_t wpos = 0;     // bytes produced
+  uint32_t flushed = 0;  // bytes already in global memory
   int fixed_ready = 0;   // the fixed tables are built in lit/dist
   int32_t st = ST_OK;
-  *produced = 0;
 
   // write window bytes of output [flushed, to) to global memory; `to` is either
   // a 16-byte boundary of the global address or the end of the output
-  auto flush = [&](uint64_t to) {
-    uint64_t f = flushed;
-    const uint64_t head_end = (((uint64_t)oaddr + f + 15) & ~15ull) - oaddr;
+  auto flush = [&](uint32_t to) {
+    uint32_t f = flushed;
+    const uint32_t head_end = ((oaddr + f + 15u) & ~15u) - oaddr;
     if (f < head_end) {  // unaligned head (first flush only)
-      const uint64_t h = (head_end < to ? head_end : to) - f;
-      if (lane < h) out[f + lane] = win[(oaddr + (uint32_t)(f + lane)) & WMASK];
+      const uint32_t h = (head_end < to ? head_end : to) - f;
+      if (lane < h) out[f + lane] = win[(oaddr + f + lane) & WMASK];
       f += h;
     }
-    const uint64_t body_end = f + ((to - f) & ~15ull);
-    for (uint64_t b = f + 16 * lane; b < body_end; b += 512) {
-      const uint4 v = *reinterpret_cast<const uint4*>(win + ((oaddr + (uint32_t)b) & WMASK));
-      *reinterpret_cast<uint4*>(out + b) = v;
-    }
+    const uint32_t body_end = f + ((to - f) & ~15u);
+    for (uint32_t b = f + 16 * lane; b < body_end; b += 512)
+      *reinterpret_cast<uint4*>(out + b) = *reinterpret_cast<const uint4*>(win + ((oaddr + b) & WMASK));
     f = body_end;
-    if (f < to && lane < to - f) out[f + lane] = win[(oaddr + (uint32_t)(f + lane)) & WMASK];
+    if (f < to && lane < to - f) out[f + lane] = win[(oaddr + f + lane) & WMASK];
     flushed = to;
+  };
+  // Far-match copies in flight: the source bytes (one per lane) are loaded
+  // from global memory when the match is decoded and written to the window
+  // later, so the load latency overlaps the decoding of later symbols.  A
+  // copy is committed before anything could read or flush its bytes.
+  struct PendingCopy {
+    uint32_t dst, len, v;
+  };
+  PendingCopy pend_a{0, 0, 0}, pend_b{0, 0, 0};  // a is the older
+  auto commit = [&](PendingCopy& p) {
+    if (p.len) {
+      if (lane < p.len) win[(oaddr + p.dst + lane) & WMASK] = (uint8_t)p.v;
+      p.len = 0;
+    }
+  };
+  auto commit_all = [&]() {
+    commit(pend_a);
+    commit(pend_b);
+  };
+  auto maybe_flush = [&]() {
+    if (STORE && !GWIN && wpos - flushed >= FLUSH_T) {
+      commit_all();
+      __syncwarp();
+      flush(((oaddr + wpos) & ~15u) - oaddr);
+      __syncwarp();
+    }
   };
 
   if (!in.refill()) return ST_TIMEOUT;
   for (;;) {
     // block header
+    if (in.nb < 32 && !in.refill()) return ST_TIMEOUT;
     if (in.avail() < 3) { st = ST_TRUNCATED; break; }
-    if (in.nb < 48 && !in.refill()) return ST_TIMEOUT;
     const uint32_t bfinal = (uint32_t)(in.bb & 1);
     const uint32_t btype = (uint32_t)((in.bb >> 1) & 3);
     in.consume(3);
     if (btype == 3) { st = ST_BAD_HEADER; break; }
-    if (btype == 0) {  // stored block
-      const uint32_t skip = (uint32_t)((8 - (in.pos & 7)) & 7);
-      if (in.avail() < (int64_t)skip + 32) { st = ST_TRUNCATED; break; }
-      in.consume(skip);
-      if (!in.refill()) return ST_TIMEOUT;
+    if (btype == 0) {  // stored block, RFC 1951 Sec. 3.2.4
+      in.consume(in.nb & 7);  // to a byte boundary
+      if (in.nb < 32 && !in.refill()) return ST_TIMEOUT;
+      if (in.avail() < 32) { st = ST_TRUNCATED; break; }
       const uint32_t len = (uint32_t)(in.bb & 0xffff);
       const uint32_t nlen = (uint32_t)((in.bb >> 16) & 0xffff);
       if (len != (~nlen & 0xffffu)) { st = ST_BAD_STORED_LEN; break; }
       if (len > limit - wpos) { st = ST_OVERFLOW; break; }
-      const int64_t src = (in.pos >> 3) + 4;
-      if (src + (int64_t)len > n_in) { st = ST_TRUNCATED; break; }
-      if (STORE) {
-        constexpr uint32_t PIECE = WIN / 4 < 1024 ? WIN / 4 : 1024;
+      in.consume(32);
+      const uint32_t src = in.byte_pos();
+      if (len > n_in - src) { st = ST_TRUNCATED; break; }
+      if (STORE && GWIN) {
+        constexpr uint32_t GPIECE = Ring::MAX_SPAN - 16 < 512 ? Ring::MAX_SPAN - 16 : 512;
+        for (uint32_t k0 = 0; k0 < len; k0 += GPIECE) {
+          const uint32_t piece = len - k0 < GPIECE ? len - k0 : GPIECE;
+          if (!ring.ensure(src + k0, src + k0 + piece + 8)) return ST_TIMEOUT;
+          for (uint32_t k = lane; k < piece; k += 32) out[wpos + k0 + k] = ring.byte(src + k0 + k);
+        }
+        __syncwarp();
+      } else if (STORE) {
+        commit_all();
+        constexpr uint32_t PIECE0 = WIN / 4 < 1024 ? WIN / 4 : 1024;
+        constexpr uint32_t PIECE = PIECE0 < Ring::MAX_SPAN - 16 ? PIECE0 : Ring::MAX_SPAN - 16;
         for (uint32_t k0 = 0; k0 < len; k0 += PIECE) {
           const uint32_t piece = len - k0 < PIECE ? len - k0 : PIECE;
-          if (!ring.ensure(src + k0, src + k0 + piece)) return ST_TIMEOUT;
-          for (uint32_t k = lane; k < piece; k += 32)
-            win[(oaddr + (uint32_t)(wpos + k0 + k)) & WMASK] = ring.byte(src + k0 + k);
+          if (!ring.ensure(src + k0, src + k0 + piece + 8)) return ST_TIMEOUT;
+          for (uint32_t k = 4 * lane; k < piece; k += 128) {
+            const uint32_t v = ring.u32(src + k0 + k);
+            const uint32_t at = oaddr + wpos + k0 + k;
+            const uint32_t n4 = piece - k < 4 ? piece - k : 4;
+            for (uint32_t t = 0; t < n4; t++) win[(at + t) & WMASK] = (uint8_t)(v >> (8 * t));
+          }
           __syncwarp();
-          const uint64_t w2 = wpos + k0 + piece;
-          if (w2 - flushed >= (uint64_t)FLUSH_T) flush((((uint64_t)oaddr + w2) & ~15ull) - oaddr);
+          const uint32_t w2 = wpos + k0 + piece;
+          if (w2 - flushed >= FLUSH_T) flush(((oaddr + w2) & ~15u) - oaddr);
           __syncwarp();
         }
       }
       wpos += len;
-      in.pos += 32 + 8 * (int64_t)len;
-      in.nb = 0;
+      in.seek_byte(src + len);
       if (!in.refill()) return ST_TIMEOUT;
     } else {
       if (btype == 1) {  // fixed codes, RFC 1951 Sec. 3.2.6
@@ -336,21 +397,28 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in,
         }
       } else {  // dynamic codes, RFC 1951 Sec. 3.2.7
         fixed_ready = 0;
+        if (in.nb < 32 && !in.refill()) return ST_TIMEOUT;
         if (in.avail() < 14) { st = ST_TRUNCATED; break; }
-        if (in.nb < 48 && !in.refill()) return ST_TIMEOUT;
         const int nlen = (int)(in.bb & 31) + 257;
         const int ndist = (int)((in.bb >> 5) & 31) + 1;
         const int ncode = (int)((in.bb >> 10) & 15) + 4;
         in.consume(14);
         if (nlen > 286 || ndist > 30) { st = ST_BAD_HUFFMAN; break; }
-        if (in.avail() < 3 * ncode) { st = ST_TRUNCATED; break; }
         if (!in.refill()) return ST_TIMEOUT;
-        // code-length code lengths; 19 x 3 = 57 bits fit one refill
-        if (lane < 19) lens[kClenOrder[lane]] = (int)lane < ncode ? (uint8_t)((in.bb >> (3 * lane)) & 7) : 0;
+        if (in.avail() < (uint32_t)(3 * ncode)) { st = ST_TRUNCATED; break; }
+        // code-length code lengths; 19 x 3 = 57 bits: two reads
+        uint64_t cl = in.bb;
+        const uint32_t first_n = ncode < 18 ? ncode : 18;
+        in.consume(3 * first_n);
+        if (ncode > 18) {
+          if (!in.refill()) return ST_TIMEOUT;
+          cl = (cl & lowmask64(54)) | ((in.bb & 7) << 54);
+          in.consume(3);
+        }
+        if (lane < 19) lens[kClenOrder[lane]] = (int)lane < ncode ? (uint8_t)((cl >> (3 * lane)) & 7) : 0;
         __syncwarp();
-        in.consume(3 * ncode);
-        HCode cl{dist_tab, dist.sorted, dist.first, dist.count, dist.offset, 0, 7, 0};
-        if (build_code(cl, lens, 19, run16) != ST_OK) { st = ST_BAD_HUFFMAN; break; }
+        HCode cl_code{dist_tab, dist.sorted, dist.first, dist.count, dist.offset, 0, 7, 0};
+        if (build_code(cl_code, lens, 19, run16) != ST_OK) { st = ST_BAD_HUFFMAN; break; }
         const int total = nlen + ndist;
         int have = 0;
         bool bad = false;
@@ -358,7 +426,7 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in,
           if (in.nb < 16 && !in.refill()) return ST_TIMEOUT;
           const uint32_t e = dist_tab[in.bb & 127];
           const uint32_t L = ent_len(e);
-          if ((int64_t)L > in.avail()) { st = ST_TRUNCATED; bad = true; break; }
+          if (L > in.avail()) { st = ST_TRUNCATED; bad = true; break; }
           if (ent_kind(e) != K_LIT) { st = ST_BAD_HUFFMAN; bad = true; break; }
           in.consume(L);
           const uint32_t sym = ent_val(e);
@@ -394,86 +462,187 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in,
         if (build_code(lit, lens, nlen, run16) != ST_OK) { st = ST_BAD_HUFFMAN; break; }
         if (build_code(dist, lens + nlen, ndist, run16) != ST_OK) { st = ST_BAD_HUFFMAN; break; }
       }
-      // symbol loop
+      // symbol loop.  Fast path while 8 input bytes and 258 output bytes
+      // remain: no code can then run past the input or the output, so only
+      // code validity and distances are checked.
       bool done = false;
       for (;;) {
+        // Lean loop for the common symbols (literals; lengths and distances
+        // whose codes fit the tables) far from both ends.  Nothing is
+        // consumed for a symbol it does not finish; the exact path below
+        // takes every other case.
+        if (GWIN && STORE) {
+          while (in.inpos + 8 <= n_in && wpos + 258 <= limit) {
+            if (in.nb < 48) {
+              if (!ring.ensure(in.inpos >= 8 ? in.inpos - 8 : 0, in.inpos + 8)) return ST_TIMEOUT;
+              in.bb |= ring.u64(in.inpos) << in.nb;
+              in.inpos += (63 - in.nb) >> 3;
+              in.nb |= 56;
+            }
+            uint32_t e = lit_tab[in.bb & LITMASK];
+            if ((int32_t)e < 0) {  // up to 3 literals (<= 45 bits)
+              uint8_t* o = out + wpos;
+              int k = 0;
+              do {
+                in.consume(e & 15u);
+                if (lane == 0) o[k] = (uint8_t)(e >> 16);
+                e = lit_tab[in.bb & LITMASK];
+              } while ((int32_t)e < 0 && ++k < 3);
+              wpos += (uint32_t)k + ((int32_t)e < 0 ? 0u : 1u);
+              continue;
+            }
+            if ((e & 0x70u) != (K_BASE << 4)) break;  // EOB, long or bad code
+            const uint32_t L = e & 15u, x = (e >> 8) & 15u;
+            const uint32_t ed = dist_tab[(in.bb >> (L + x)) & DISTMASK];
+            if ((ed & 0x70u) != (K_BASE << 4)) break;
+            const uint32_t Ld = ed & 15u, xd = (ed >> 8) & 15u;
+            const uint32_t mlen = ((e >> 16) & 0x7fffu) + ((uint32_t)(in.bb >> L) & ((1u << x) - 1));
+            const uint32_t d = ((ed >> 16) & 0x7fffu) +
+                               ((uint32_t)(in.bb >> (L + x + Ld)) & ((1u << xd) - 1));
+            if (d > wpos) break;  // the exact path reports BAD_DISTANCE
+            in.consume(L + x + Ld + xd);
+            uint8_t* o = out + wpos;
+            const uint8_t* src = o - d;
+            __syncwarp();
+            if (d >= mlen) {
+              for (uint32_t i = lane; i < mlen; i += 32) o[i] = src[i];
+            } else {  // overlap: byte i repeats source byte i mod d (exact float division here)
+              const float r = __frcp_ru((float)d);
+              uint32_t kk = lane - d * (uint32_t)__float2uint_rz((float)lane * r);
+              const uint32_t step = 32u - d * (uint32_t)__float2uint_rz(32.0f * r);
+              for (uint32_t i = lane; i < mlen; i += 32) {
+                o[i] = src[kk];
+                kk += step;
+                if (kk >= d) kk -= d;
+              }
+            }
+            wpos += mlen;
+          }
+        }
+        const bool fast = in.inpos + 8 <= n_in && wpos + 258 <= limit;
         if (in.nb < 48 && !in.refill()) return ST_TIMEOUT;
-        uint32_t e = lit_tab[in.bb & ((1u << LIT_TB) - 1)];
+        uint32_t e = lit_tab[in.bb & LITMASK];
+        if (fast && ent_kind(e) == K_LIT) {  // up to 3 literals per refill (<= 45 bits)
+          int k = 0;
+          do {
+            in.consume(ent_len(e));
+            if (STORE && lane == 0) {
+              if (GWIN) out[wpos] = (uint8_t)ent_val(e);
+              else win[(oaddr + wpos) & WMASK] = (uint8_t)ent_val(e);
+            }
+            wpos++;
+            e = lit_tab[in.bb & LITMASK];
+          } while (ent_kind(e) == K_LIT && ++k < 3);
+          maybe_flush();
+          continue;
+        }
         if (ent_kind(e) == K_LONG) e = decode_long(lit, in.bb);
         uint32_t L = ent_len(e);
         uint32_t kind = ent_kind(e);
-        if ((int64_t)L > in.avail()) { st = ST_TRUNCATED; break; }
-        if (kind == K_BADCODE || kind == K_BADSYM) { st = ST_BAD_HUFFMAN; break; }
+        if (!fast && L > in.avail()) { st = ST_TRUNCATED; break; }
+        if (kind >= K_BADSYM) { st = ST_BAD_HUFFMAN; break; }
         in.consume(L);
         if (kind == K_LIT) {
-          if (wpos >= limit) { st = ST_OVERFLOW; break; }
-          if (STORE && lane == 0) win[(oaddr + (uint32_t)wpos) & WMASK] = (uint8_t)ent_val(e);
-          wpos++;
-          if (STORE && wpos - flushed >= (uint64_t)FLUSH_T) {
-            __syncwarp();
-            flush((((uint64_t)oaddr + wpos) & ~15ull) - oaddr);
-            __syncwarp();
+          if (!fast && wpos >= limit) { st = ST_OVERFLOW; break; }
+          if (STORE && lane == 0) {
+            if (GWIN) out[wpos] = (uint8_t)ent_val(e);
+            else win[(oaddr + wpos) & WMASK] = (uint8_t)ent_val(e);
           }
+          wpos++;
+          maybe_flush();
           continue;
         }
         if (kind == K_EOB) { done = true; break; }
         // length
         uint32_t x = ent_extra(e);
-        if ((int64_t)x > in.avail()) { st = ST_TRUNCATED; break; }
+        if (!fast && x > in.avail()) { st = ST_TRUNCATED; break; }
         const uint32_t mlen = ent_val(e) + (uint32_t)(in.bb & ((1u << x) - 1));
         in.consume(x);
         // distance
-        e = dist_tab[in.bb & ((1u << DIST_TB) - 1)];
+        e = dist_tab[in.bb & DISTMASK];
         if (ent_kind(e) == K_LONG) e = decode_long(dist, in.bb);
         L = ent_len(e);
         kind = ent_kind(e);
-        if ((int64_t)L > in.avail()) { st = ST_TRUNCATED; break; }
-        if (kind == K_BADCODE || kind == K_BADSYM) { st = ST_BAD_HUFFMAN; break; }
+        if (!fast && L > in.avail()) { st = ST_TRUNCATED; break; }
+        if (kind >= K_BADSYM) { st = ST_BAD_HUFFMAN; break; }
         in.consume(L);
         x = ent_extra(e);
-        if ((int64_t)x > in.avail()) { st = ST_TRUNCATED; break; }
+        if (!fast && x > in.avail()) { st = ST_TRUNCATED; break; }
         const uint32_t d = ent_val(e) + (uint32_t)(in.bb & ((1u << x) - 1));
         in.consume(x);
-        if ((uint64_t)d > wpos) { st = ST_BAD_DISTANCE; break; }
-        if ((uint64_t)mlen > limit - wpos) { st = ST_OVERFLOW; break; }
-        if (STORE) {
+        if (d > wpos) { st = ST_BAD_DISTANCE; break; }
+        if (!fast && mlen > limit - wpos) { st = ST_OVERFLOW; break; }
+        if (STORE && GWIN) {
+          // source bytes are earlier output of this warp, in global memory
+          const uint32_t s0 = wpos - d;
           __syncwarp();
-          const uint64_t s0 = wpos - d;
-          if ((int64_t)d <= NEAR_MAX) {
+          if (d >= mlen) {
+            for (uint32_t i = lane; i < mlen; i += 32) out[wpos + i] = out[s0 + i];
+          } else {  // overlap: byte i repeats source byte i mod d
+            uint32_t k = lane % d;
+            const uint32_t step = 32 % d;
             for (uint32_t i = lane; i < mlen; i += 32) {
-              const uint32_t k = d >= mlen ? i : i % d;
-              win[(oaddr + (uint32_t)(wpos + i)) & WMASK] = win[(oaddr + (uint32_t)(s0 + k)) & WMASK];
+              out[wpos + i] = out[s0 + k];
+              k += step;
+              if (k >= d) k -= d;
             }
-          } else {  // far source: already flushed to global memory
-            for (uint32_t i = lane; i < mlen; i += 32)
-              win[(oaddr + (uint32_t)(wpos + i)) & WMASK] = __ldcg(out + s0 + i);
           }
-          __syncwarp();
+        } else if (STORE) {
+          const uint32_t s0 = wpos - d;
+          if (d > NEAR_MAX && mlen <= 32) {
+            // far source, already in global memory: load now, write later
+            if (pend_a.len && pend_b.len) {  // both slots busy: retire the older
+              commit(pend_a);
+              pend_a = pend_b;
+              pend_b.len = 0;
+            }
+            const PendingCopy nw{wpos, mlen, lane < mlen ? (uint32_t)__ldcg(out + s0 + lane) : 0u};
+            if (!pend_a.len) pend_a = nw;
+            else pend_b = nw;
+          } else if (d > NEAR_MAX) {  // long far copy: synchronous
+            commit_all();
+            for (uint32_t i = lane; i < mlen; i += 32)
+              win[(oaddr + wpos + i) & WMASK] = __ldcg(out + s0 + i);
+            __syncwarp();
+          } else {
+            // near source in the window; it may overlap a pending far copy
+            const uint32_t rd_end = s0 + (d < mlen ? d : mlen);
+            if ((pend_a.len && s0 < pend_a.dst + pend_a.len && pend_a.dst < rd_end) ||
+                (pend_b.len && s0 < pend_b.dst + pend_b.len && pend_b.dst < rd_end))
+              commit_all();
+            __syncwarp();
+            if (d >= mlen) {
+              for (uint32_t i = lane; i < mlen; i += 32)
+                win[(oaddr + wpos + i) & WMASK] = win[(oaddr + s0 + i) & WMASK];
+            } else {  // overlap: byte i repeats source byte i mod d
+              uint32_t k = lane % d;
+              const uint32_t step = 32 % d;
+              for (uint32_t i = lane; i < mlen; i += 32) {
+                win[(oaddr + wpos + i) & WMASK] = win[(oaddr + s0 + k) & WMASK];
+                k += step;
+                if (k >= d) k -= d;
+              }
+            }
+          }
         }
         wpos += mlen;
-        if (STORE && wpos - flushed >= (uint64_t)FLUSH_T) {
-          __syncwarp();
-          flush((((uint64_t)oaddr + wpos) & ~15ull) - oaddr);
-          __syncwarp();
-        }
+        maybe_flush();
       }
       if (!done) break;
     }
-    if (STORE && wpos - flushed >= (uint64_t)FLUSH_T) {
-      __syncwarp();
-      flush((((uint64_t)oaddr + wpos) & ~15ull) - oaddr);
-      __syncwarp();
-    }
+    maybe_flush();
     if (bfinal) break;
   }
-  if (STORE) {
+  if (STORE && !GWIN) {
+    commit_all();
     __syncwarp();
     if (wpos > flushed) flush(wpos);
     __syncwarp();
   }
+  if (STORE && GWIN) __syncwarp();
   *produced = wpos;
   if (st != ST_OK) return st;
-  if (STORE && wpos < cap) return ST_UNDERFLOW;
+  if (STORE && wpos < limit) return ST_UNDERFLOW;
   return ST_OK;
 }
 

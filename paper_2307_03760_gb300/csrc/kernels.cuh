@@ -21,8 +21,8 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
 
 using RleRing = InRing<1024, 4>;
-using DeflateRing = InRing<512, 4>;
-constexpr int kLitTB = 10, kDistTB = 8, kWin = 4096;
+using DeflateRing = InRing<256, 4>;
+constexpr int kLitTB = 10, kDistTB = 8, kWin = 0;
 using DeflateSmem = InflateSmem<kLitTB, kDistTB, kWin>;
 
 constexpr int round128(int x) { return (x + 127) & ~127; }
