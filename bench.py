@@ -289,6 +289,9 @@ def main():
     ap.add_argument("--workload", default="rle_v2", choices=list(WORKLOAD_DESC))
     ap.add_argument("--no-per-format", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="arrival window per request rate in the serving sweep")
     ap.add_argument("--parts", type=int, default=0,
                     help="parts per RLE chunk (0 = library default)")
     ap.add_argument("--scale", type=float, default=1.0,
@@ -405,6 +408,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_per_format:
         line["per_format"] = per_format(torch, codag, dev, stream, peak, name, w, d, value, achieved)
 
+    if rank == 0 and world == 1 and not args.no_serving:
+        line["serving"] = serving(torch, args.serve_seconds)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, reps, el = oracle_rate(w, FMT_OF.get(name, 0), seconds=10.0)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "GB/s", "cores": threads,
@@ -415,6 +421,38 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving(torch, seconds: float):
+    """Continuous-batching server under Poisson arrivals: requests of 1-256
+    chunks of one random format, 64 KiB-64 MiB decoded, 32 GiB HBM budget.
+    Latency = arrival -> completion seen by the host, including the copy of
+    the request's compressed bytes from pinned host memory."""
+    from paper_2307_03760_gb300.serve import Request, Server
+    pool = synth.serving_pool(seed=1, n_payloads=32)
+    pinned = [torch.from_numpy(w.comp).pin_memory() for w in pool]
+    mean_bytes = float(np.mean([w.out_bytes for w in pool]))
+    srv = Server(budget=32 << 30, streams=4, max_batch_chunks=32768)
+    # warm the path once
+    warm = [Request(0, pool[0].formats, pool[0].comp, pool[0].comp_off, pool[0].out_off, 0.0)]
+    srv.run(warm, {0: pinned[0]}, time_limit=10.0)
+    srv.drain()
+    out = {"payloads": len(pool), "mean_request_bytes": int(mean_bytes),
+           "budget_bytes": 32 << 30, "streams": 4, "rates": {}}
+    for lam in (1000, 2000, 5000, 10000, 20000, 50000):
+        times, pick = synth.poisson_arrivals(1, float(lam), seconds, len(pool))
+        times, pick = times[:20000], pick[:20000]
+        reqs = [Request(i, pool[p].formats, pool[p].comp, pool[p].comp_off, pool[p].out_off,
+                        float(t)) for i, (t, p) in enumerate(zip(times, pick))]
+        inputs = {r.rid: pinned[p] for r, p in zip(reqs, pick)}
+        st = srv.run(reqs, inputs, time_limit=seconds + 4.0)
+        summ = st.summary()
+        summ["offered_GBps"] = round(lam * mean_bytes / 1e9, 2)
+        summ["requests"] = len(reqs)
+        summ["errors"] = int(sum(int((r.status != 0).any()) for r in reqs if r.status is not None))
+        out["rates"][str(lam)] = summ
+        srv.drain()
+    return out
 
 
 def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):

@@ -158,6 +158,20 @@ codag_status codag_decompress_batch(const uint8_t *formats, const void *comp,
 codag_status codag_last_chunk_status(int32_t *host_status, uint64_t n, cudaStream_t stream);
 
 /*
+ * codag_decompress_batch_ws - codag_decompress_batch with caller-provided
+ * scratch (device memory, 256-byte aligned, at least
+ * codag_batch_scratch_bytes(n_chunks) bytes) instead of the shared library
+ * workspace, so that batches on several streams may run at the same time
+ * (each with its own scratch).  chunk_status is required.  Nothing is
+ * allocated; the scratch is only used by the work this call enqueues.
+ */
+uint64_t codag_batch_scratch_bytes(uint64_t n_chunks);
+codag_status codag_decompress_batch_ws(const uint8_t *formats, const void *comp,
+                                       const uint64_t *comp_offsets, uint64_t n_chunks, void *out,
+                                       const uint64_t *out_offsets, int32_t *chunk_status,
+                                       void *scratch, uint64_t scratch_bytes, cudaStream_t stream);
+
+/*
  * codag_decompress_batch_noalloc - the batch decode above, for callers that
  * cannot let a library allocate device memory: programs that budget or pool
  * every byte of device memory themselves, and latency-critical loops that

@@ -58,6 +58,9 @@ def lib() -> ctypes.CDLL:
         L.codag_decompress_batch.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
         L.codag_last_chunk_status.argtypes = [vp, u64, vp]
         L.codag_decompress_batch_noalloc.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
+        L.codag_decompress_batch_ws.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp, u64, vp]
+        L.codag_batch_scratch_bytes.argtypes = [u64]
+        L.codag_batch_scratch_bytes.restype = u64
         L.codag_batch_graph_create.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp, ctypes.POINTER(vp)]
         L.codag_batch_graph_launch.argtypes = [vp, vp]
         L.codag_batch_graph_destroy.argtypes = [vp]
@@ -68,7 +71,7 @@ def lib() -> ctypes.CDLL:
                      "codag_last_chunk_status", "codag_batch_graph_create",
                      "codag_batch_graph_launch", "codag_batch_graph_destroy",
                      "codag_set_batch_ctas_per_sm", "codag_decompress_batch_noalloc",
-                     "codag_set_parts_per_chunk"):
+                     "codag_set_parts_per_chunk", "codag_decompress_batch_ws"):
             getattr(L, name).restype = i32
         L.codag_get_batch_ctas_per_sm.restype = i32
         L.codag_kernel_launches.restype = ctypes.c_uint64
@@ -121,6 +124,20 @@ def codag_decompress_batch(formats, comp, comp_offsets, n_chunks: int, out, out_
     _check(lib().codag_decompress_batch(_ptr(formats), _ptr(comp), _ptr(comp_offsets), n_chunks,
                                         _ptr(out), _ptr(out_offsets), _ptr(chunk_status),
                                         _stream(stream)), "codag_decompress_batch")
+
+
+def codag_batch_scratch_bytes(n_chunks: int) -> int:
+    return lib().codag_batch_scratch_bytes(n_chunks)
+
+
+def codag_decompress_batch_ws(formats, comp, comp_offsets, n_chunks: int, out, out_offsets,
+                              chunk_status, scratch, scratch_bytes: int, stream=None):
+    """Batch decode with caller-provided scratch (so batches on several
+    streams can run concurrently)."""
+    _check(lib().codag_decompress_batch_ws(_ptr(formats), _ptr(comp), _ptr(comp_offsets), n_chunks,
+                                           _ptr(out), _ptr(out_offsets), _ptr(chunk_status),
+                                           _ptr(scratch), scratch_bytes, _stream(stream)),
+           "codag_decompress_batch_ws")
 
 
 def codag_decompress_batch_noalloc(formats, comp, comp_offsets, n_chunks: int, out, out_offsets,

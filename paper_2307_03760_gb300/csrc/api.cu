@@ -280,6 +280,35 @@ codag_status codag_decompress_batch(const uint8_t* formats, const void* comp,
                        w->order, w->keys, w->counters, stream);
 }
 
+uint64_t codag_batch_scratch_bytes(uint64_t n_chunks) {
+  // keys (8 per chunk), counters (256-byte block), order (4 per chunk)
+  return n_chunks * 8 + 256 * ((kBatchCounterWords * 4 + 255) / 256) + n_chunks * 4 + 256;
+}
+
+codag_status codag_decompress_batch_ws(const uint8_t* formats, const void* comp,
+                                       const uint64_t* comp_offsets, uint64_t n_chunks, void* out,
+                                       const uint64_t* out_offsets, int32_t* chunk_status,
+                                       void* scratch, uint64_t scratch_bytes, cudaStream_t stream) {
+  if (n_chunks == 0) return CODAG_OK;
+  codag_status s = check_batch(formats, comp, comp_offsets, n_chunks, out, out_offsets);
+  if (s != CODAG_OK) return s;
+  if (!chunk_status || !scratch) return fail(CODAG_EINVAL, "NULL chunk_status or scratch");
+  if (reinterpret_cast<uintptr_t>(scratch) & 255) return fail(CODAG_EINVAL, "scratch must be 256-byte aligned");
+  if (scratch_bytes < codag_batch_scratch_bytes(n_chunks))
+    return fail(CODAG_EINVAL, "scratch smaller than codag_batch_scratch_bytes(n_chunks)");
+  uint8_t* base = static_cast<uint8_t*>(scratch);
+  unsigned long long* keys = reinterpret_cast<unsigned long long*>(base);
+  uint32_t* counters = reinterpret_cast<uint32_t*>(base + ((n_chunks * 8 + 255) & ~255ull));
+  uint32_t* order = counters + 64 * ((kBatchCounterWords + 63) / 64);
+  Workspace* w;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if ((s = current_ws(&w)) != CODAG_OK) return s;
+  }
+  return enqueue_batch(*w, formats, comp, comp_offsets, n_chunks, out, out_offsets, chunk_status,
+                       order, keys, counters, stream);
+}
+
 codag_status codag_last_chunk_status(int32_t* host_status, uint64_t n, cudaStream_t stream) {
   if (n == 0) return CODAG_OK;
   if (!host_status) return fail(CODAG_EINVAL, "NULL host_status");

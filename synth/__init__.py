@@ -197,3 +197,30 @@ def batched_plan(seed: int = 1, n_chunks: int = 20000, lo: int = 4096, hi: int =
 def batched(seed: int = 1, n_chunks: int = 20000, lo: int = 4096, hi: int = MiB, **kw) -> Chunked:
     fmts, sizes = batched_plan(seed, n_chunks, lo, hi)
     return build_chunks(fmts, sizes, seed, name="batched", **kw)
+
+
+def serving_pool(seed: int = 1, n_payloads: int = 32, lo: int = 64 * 1024, hi: int = 64 * MiB,
+                 keep_plain: bool = False, threads: int | None = None):
+    """Request payloads for the serving workload: each a random format (RLE
+    v1, RLE v2 or Deflate, uniform), total decoded size log-uniform in
+    [lo, hi), 1-256 chunks of equal size (multiples of 8 bytes)."""
+    g = np.random.Generator(np.random.PCG64(seed * 104729 + 5))
+    pool = []
+    for p in range(n_payloads):
+        fmt = int(g.choice([RLE_V1_I64, RLE_V2_I64, DEFLATE]))
+        total = int(np.exp(g.uniform(np.log(lo), np.log(hi))))
+        n = int(g.integers(1, 257))
+        size = max(8, total // n // 8 * 8)
+        pool.append(build_chunks([fmt] * n, [size] * n, seed * 1000 + p, keep_plain=keep_plain,
+                                 threads=threads, name=f"payload{p}"))
+    return pool
+
+
+def poisson_arrivals(seed: int, rate: float, duration: float, n_payloads: int):
+    """Arrival times (seconds) of a Poisson process of `rate` requests/s over
+    `duration` seconds, and the payload each request carries."""
+    g = np.random.Generator(np.random.PCG64(seed * 7 + int(rate)))
+    n = max(1, int(rate * duration * 1.5) + 16)
+    t = np.cumsum(g.exponential(1.0 / rate, n))
+    t = t[t < duration]
+    return t, g.integers(0, n_payloads, len(t))
