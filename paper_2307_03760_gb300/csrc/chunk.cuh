@@ -118,13 +118,31 @@ __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, 
   return r;
 }
 
-// Plain RLE kernels: one CTA per chunk; its K warps decode the K parts and
-// combine their statuses in shared memory.  Shared memory: [stage][K scratch]
-// [mbarrier][key][split table].  A chunk that fits the stage is copied in
-// whole by TMA (issued by warp 0, one mbarrier); warp 0 walks it once to find
-// where the parts start, then every part decodes its runs in place.  A larger
-// chunk is streamed: warp 0 walks it through a ring, then each part streams
-// its own sub-stream through a ring of its own carved from the stage area.
+// Wait (bounded) until at least k + 1 segment starts are published.
+__device__ __forceinline__ bool wait_published(volatile uint32_t* published, uint32_t k) {
+  if (*published > k) return true;
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t polls = 0; polls < kMaxWaitPolls; polls++) {
+    __nanosleep(128);
+    if (*published > k) return true;
+    if (globaltimer_ns() - t0 > kMaxWaitNs) return false;
+  }
+  return false;
+}
+
+// Plain RLE kernels: one CTA per chunk, K warps.  Shared memory:
+// [stage][K scratch][mbarrier][key][published][claimed][segment tables].
+//
+// A chunk that fits the stage is copied in whole by TMA (warp 0, one
+// mbarrier).  Its output is cut into nseg segments of about equal numbers of
+// values.  Warp 0 walks the run headers once and publishes where each
+// segment starts (a run boundary) as soon as its walk reaches it; every warp,
+// warp 0 included once its walk is done, claims segments with an atomic
+// counter and decodes each one in place as soon as its start is known.
+// Statuses combine by an atomic minimum over (stream position, code).
+//
+// A larger chunk is streamed: warp 0 walks it through a ring to the K part
+// starts, then each warp streams its own part through a ring of its own.
 template <int FAMILY, bool STORE>
 __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -135,9 +153,11 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   uint8_t* scratch = smem + stage_bytes + warp * kRleScratch;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + K * kRleScratch);
   unsigned long long* key = reinterpret_cast<unsigned long long*>(bar + 1);
-  int64_t* split_pos = reinterpret_cast<int64_t*>(bar + 2);  // [17]
-  uint64_t* split_cnt = reinterpret_cast<uint64_t*>(split_pos + 17);  // [17]
-  uint64_t* target = split_cnt + 17;  // [17]
+  uint32_t* published = reinterpret_cast<uint32_t*>(bar + 2);
+  uint32_t* claimed = published + 1;
+  int64_t* split_pos = reinterpret_cast<int64_t*>(bar + 3);      // [kMaxSeg + 1]
+  uint64_t* split_cnt = reinterpret_cast<uint64_t*>(split_pos + kMaxSeg + 1);
+  uint64_t* target = split_cnt + kMaxSeg + 1;
   const ChunkGeom g = chunk_geom<FAMILY, STORE>(a, c);
   if (g.bad != ST_OK) {
     if (threadIdx.x == 0) {
@@ -152,8 +172,16 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   const int64_t skew = chunk - gsrc;
   const bool staged = staged_bytes(g.n_in) <= stage_bytes;
   const uint64_t cap_v = g.cap / 8;
+  // segments: about kSegValues values each, at least K, at most kMaxSeg
+  uint32_t nseg = K;
+  if (staged && STORE) {
+    const uint64_t want = cap_v / kSegValues;
+    nseg = want < K ? K : want > (uint64_t)kMaxSeg ? (uint32_t)kMaxSeg : (uint32_t)want;
+  }
   if (threadIdx.x == 0) {
     *key = ~0ull;
+    *published = 1;
+    *claimed = 0;
     split_pos[0] = 0;
     split_cnt[0] = 0;
     if (staged) {
@@ -162,9 +190,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
       fence_proxy_async_smem();
     }
   }
-  if (threadIdx.x < K) target[threadIdx.x] = part_target(cap_v, threadIdx.x, K);
+  for (uint32_t t = threadIdx.x; t <= nseg; t += blockDim.x) target[t] = part_target(cap_v, t, nseg);
   __syncthreads();
-  PartResult r;
   if (staged) {
     // readable: [gsrc, buf_end); copy up to the chunk end rounded to 16
     int64_t bytes = (skew + g.n_in + 15) & ~int64_t(15);
@@ -185,20 +212,34 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     if (!ok) ok = mbar_wait_bounded(bar, 0);  // second bounded wait for the copies in flight
     __syncthreads();  // also publishes warp 0's tail bytes
     StagedInput in{stage, gsrc, skew};
-    if (ok && warp == 0 && K > 1) {
-      if (FAMILY == 1)
-        rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
-                    split_pos, split_cnt);
-      else
-        rle_v2_walk(in, g.n_in, target, (int)K - 1, split_pos, split_cnt);
-    }
-    __syncthreads();
     if (!ok) {
-      r = PartResult{ST_TIMEOUT, 0, 0};
+      if (threadIdx.x == 0) *key = status_key(PartResult{ST_TIMEOUT, 0, 0});
     } else {
-      const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
-      r = decode_rle_part<FAMILY, STORE>(in, scratch, a, g, a.format, split_pos[warp],
-                                         split_cnt[warp], hi);
+      if (warp == 0 && nseg > 1) {
+        if (FAMILY == 1)
+          rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)nseg - 1,
+                      split_pos, split_cnt, published);
+        else
+          rle_v2_walk(in, g.n_in, target, (int)nseg - 1, split_pos, split_cnt, published);
+      }
+      for (;;) {
+        uint32_t k = 0;
+        if (lane_id() == 0) k = atomicAdd(claimed, 1u);
+        k = __shfl_sync(FULL, k, 0);
+        if (k >= nseg) break;
+        PartResult r;
+        if (!wait_published(published, k)) {
+          r = PartResult{ST_TIMEOUT, 0, 0};
+        } else {
+          __threadfence_block();
+          const uint64_t hi = k + 1 < nseg ? target[k + 1] : ~0ull;
+          r = decode_rle_part<FAMILY, STORE>(in, scratch, a, g, a.format, split_pos[k],
+                                             split_cnt[k], hi);
+        }
+        if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
+        if (!STORE && k + 1 == nseg && lane_id() == 0) a.sizes[c] = r.count;
+        if (r.status == ST_TIMEOUT) break;
+      }
     }
   } else {
     RleRing ring;
@@ -220,14 +261,14 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     sub.n_in = g.n_in - base;
     ring.start(chunk + base, sub.n_in, buf_end);
     const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
-    r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, sub, a.format, 0, split_cnt[warp], hi);
+    PartResult r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, sub, a.format, 0, split_cnt[warp], hi);
     if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
     if (!ring.drain() || !ok) r.status = ST_TIMEOUT;
+    if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
+    if (!STORE && warp == K - 1 && lane_id() == 0) a.sizes[c] = r.count;
   }
-  if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
   __syncthreads();
   if (threadIdx.x == 0) a.status[c] = key_status(*key);
-  if (!STORE && warp == K - 1 && lane_id() == 0) a.sizes[c] = r.count;
 }
 
 // Plain Deflate kernel: one warp per chunk.

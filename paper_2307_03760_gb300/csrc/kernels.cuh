@@ -36,8 +36,12 @@ constexpr int kRleScratch = 512;
 // plain RLE kernels: whole-chunk staging area per CTA (chunks up to about
 // 32 KiB compressed are staged in one piece) and the largest launch
 constexpr int kRleStageBytes = 32768 + 256;
-// per-CTA extras: mbarrier, status key, split positions/counts/targets
-constexpr int kRleCtaExtra = 16 + 3 * 17 * 8;
+// segments of a staged RLE chunk: about kSegValues values each, at most kMaxSeg
+constexpr int kMaxSeg = 64;
+constexpr int kSegValues = 1024;
+// per-CTA extras: mbarrier, status key, published/claimed, split positions,
+// counts and targets
+constexpr int kRleCtaExtra = 24 + 3 * (kMaxSeg + 1) * 8;
 constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra;
 constexpr int kBatchWarp =
     round128(RleRing::SMEM + cmax(DeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));

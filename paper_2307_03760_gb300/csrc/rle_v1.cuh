@@ -146,21 +146,33 @@ __device__ __forceinline__ int32_t v1_parse_group(In& in, int64_t pos, int64_t n
   return ST_OK;
 }
 
+// When `published` is given, split k is made visible to the CTA's other
+// warps as soon as it is known (*published = k + 1 after a block fence).
+__device__ __forceinline__ void publish_split(int k, int64_t pos, uint64_t count, int64_t* split_pos,
+                                              uint64_t* split_cnt, volatile uint32_t* published) {
+  if (lane_id() == 0) {
+    split_pos[k] = pos;
+    split_cnt[k] = count;
+    if (published) {
+      __threadfence_block();
+      *published = (uint32_t)k + 1;
+    }
+  }
+}
+
 // Walk an RLE v1 stream's groups (one warp) and record where parts start;
 // same contract as rle_v2_walk.
 template <class In>
 __device__ __forceinline__ void rle_v1_walk(In& in, uint16_t* ends, int64_t n_in,
                                             const uint64_t* target, int nsplit, int64_t* split_pos,
-                                            uint64_t* split_cnt) {
+                                            uint64_t* split_cnt,
+                                            volatile uint32_t* published = nullptr) {
   int64_t pos = 0;
   uint64_t count = 0;
   int k = 1;
   while (pos < n_in && k <= nsplit) {
     while (k <= nsplit && count >= target[k]) {
-      if (lane_id() == 0) {
-        split_pos[k] = pos;
-        split_cnt[k] = count;
-      }
+      publish_split(k, pos, count, split_pos, split_cnt, published);
       k++;
     }
     if (k > nsplit) break;
@@ -171,11 +183,7 @@ __device__ __forceinline__ void rle_v1_walk(In& in, uint16_t* ends, int64_t n_in
     count += gr.len;
     pos = gr.end;
   }
-  for (; k <= nsplit; k++)
-    if (lane_id() == 0) {
-      split_pos[k] = pos;
-      split_cnt[k] = count;
-    }
+  for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
 // Decode part of one RLE v1 chunk; same contract as rle_v2_part.

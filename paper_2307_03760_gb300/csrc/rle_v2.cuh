@@ -135,16 +135,14 @@ __device__ __forceinline__ int32_t v2_parse_run(const In& in, int64_t pos, int64
 // so the last part finds the error again.  split_pos / split_cnt: shared.
 template <class In>
 __device__ __forceinline__ void rle_v2_walk(In& in, int64_t n_in, const uint64_t* target,
-                                            int nsplit, int64_t* split_pos, uint64_t* split_cnt) {
+                                            int nsplit, int64_t* split_pos, uint64_t* split_cnt,
+                                            volatile uint32_t* published = nullptr) {
   int64_t pos = 0;
   uint64_t count = 0;
   int k = 1;
   while (pos < n_in && k <= nsplit) {
     while (k <= nsplit && count >= target[k]) {
-      if (lane_id() == 0) {
-        split_pos[k] = pos;
-        split_cnt[k] = count;
-      }
+      publish_split(k, pos, count, split_pos, split_cnt, published);
       k++;
     }
     if (k > nsplit) break;
@@ -154,11 +152,7 @@ __device__ __forceinline__ void rle_v2_walk(In& in, int64_t n_in, const uint64_t
     count += r.len;
     pos = r.end;
   }
-  for (; k <= nsplit; k++)
-    if (lane_id() == 0) {
-      split_pos[k] = pos;
-      split_cnt[k] = count;
-    }
+  for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
 // Decode part of one RLE v2 chunk.  The part's stream starts at a run
