@@ -283,7 +283,7 @@ def split_by_format(w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="codag", choices=["codag", "reference"])
     ap.add_argument("--workload", default="rle_v2", choices=list(WORKLOAD_DESC))
@@ -294,6 +294,8 @@ def main():
                     help="arrival window per request rate in the serving sweep")
     ap.add_argument("--parts", type=int, default=0,
                     help="parts per RLE chunk (0 = library default)")
+    ap.add_argument("--no-tuning", action="store_true",
+                    help="ignore the committed autotuner table")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="workload size factor; 1.0 is the measured configuration")
     args = ap.parse_args()
@@ -318,6 +320,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     codag.lib()
+    from paper_2307_03760_gb300 import autotune
+    tuned = autotune.apply(n_chunks=None, family=args.workload) if not args.no_tuning else {}
     if args.parts:
         codag.codag_set_parts_per_chunk(args.parts)
     stream = torch.cuda.current_stream()
@@ -396,7 +400,8 @@ def main():
                    "uncompressed_bytes": w.out_bytes, "ratio": round(w.comp_bytes / w.out_bytes, 4),
                    "l2": "inputs+outputs larger than L2 (no flush)", "seed": 1,
                    "parallelism": f"chunk-parallel x{world} (independent columns per GPU)",
-                   "parts_per_chunk": codag.codag_get_parts_per_chunk() or "auto"},
+                   "parts_per_chunk": codag.codag_get_parts_per_chunk() or "auto",
+                   "tuning": tuned},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": w.comp_bytes + 16 * (w.n + 1),
                 "d2h_bytes_per_step": w.out_bytes, "output_checked": bool(ok)},
@@ -467,7 +472,7 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
         fn()
         torch.cuda.synchronize()
         st = codag.codag_last_chunk_status(w.n)
-        ms = time_steps(torch, stream, fn, 20 if name == "rle_v1" else 10, 3)
+        ms = time_steps(torch, stream, fn, 100 if name == "rle_v1" else 10, 3)
         t = statistics.median(ms)
         res[name] = {"GBps": round(w.out_bytes / (t / 1e3) / 1e9, 2),
                      "hbm_frac": round(d.alg_bytes() / (t / 1e3) / 1e9 / peak, 4),
