@@ -80,10 +80,13 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1) -> dict:
         table["rle_parts"][name] = {"chunks": w.n, "best": best, "ms": round(ms, 4)}
         table["sweeps"][f"{name}_parts"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}
     codag.codag_set_parts_per_chunk(0)
-    w = synth.batched(seed, n_chunks=5000)
+    # the full mixed batch: a sample of it would be dominated by its largest
+    # chunk and favour too few CTAs
+    w = synth.batched(seed)
     comp, coff, ooff, fm, out, st = upload(w)
     run = lambda: codag.codag_decompress_batch(fm, comp, coff, w.n, out, ooff, st)  # noqa: E731
-    t = sweep(run, [1, 2, 3, 4, 6, 8], codag.codag_set_batch_ctas_per_sm, reps=5, timer=timer)
+    t = sweep(run, [1, 2, 3, 4, 5, 6, 8], codag.codag_set_batch_ctas_per_sm, reps=3, warmup=1,
+              timer=timer)
     best, ms = choose(t)
     table["batch_ctas_per_sm"] = {"best": best, "ms": round(ms, 3), "chunks": w.n}
     table["sweeps"]["batch_ctas_per_sm"] = {str(k): round(statistics.median(v), 3) for k, v in t.items()}
