@@ -61,13 +61,67 @@ __device__ __forceinline__ uint32_t dist_sym_entry(uint32_t len, uint32_t d) {
   return make_ent(len, K_BASE, e, ((2u + (d & 1u)) << e) + 1u);
 }
 
+// Shared-memory tables hold 16-bit entries: bits 0-3 code length, 4-11 value
+// (literal byte, length-symbol index 0-28, distance code 0-29, or
+// code-length symbol), 12-14 kind, bit 15 set for literals.  Base and extra
+// bits of lengths and distances come from the two small constant tables
+// below (all lanes read the same entry, a broadcast).
+constexpr uint32_t len_info(uint32_t i) {  // base | extra << 16, RFC 1951 Sec. 3.2.5
+  return i < 8 ? 3 + i : i == 28 ? 258u
+                       : ((((4u + (i & 3u)) << ((i >> 2) - 1)) + 3u) | (((i >> 2) - 1) << 16));
+}
+constexpr uint32_t dist_info(uint32_t d) {
+  return d < 4 ? 1 + d : ((((2u + (d & 1u)) << ((d >> 1) - 1)) + 1u) | (((d >> 1) - 1) << 16));
+}
+static __constant__ uint32_t kLenInfo[29] = {
+    len_info(0),  len_info(1),  len_info(2),  len_info(3),  len_info(4),  len_info(5),
+    len_info(6),  len_info(7),  len_info(8),  len_info(9),  len_info(10), len_info(11),
+    len_info(12), len_info(13), len_info(14), len_info(15), len_info(16), len_info(17),
+    len_info(18), len_info(19), len_info(20), len_info(21), len_info(22), len_info(23),
+    len_info(24), len_info(25), len_info(26), len_info(27), len_info(28)};
+static __constant__ uint32_t kDistInfo[30] = {
+    dist_info(0),  dist_info(1),  dist_info(2),  dist_info(3),  dist_info(4),  dist_info(5),
+    dist_info(6),  dist_info(7),  dist_info(8),  dist_info(9),  dist_info(10), dist_info(11),
+    dist_info(12), dist_info(13), dist_info(14), dist_info(15), dist_info(16), dist_info(17),
+    dist_info(18), dist_info(19), dist_info(20), dist_info(21), dist_info(22), dist_info(23),
+    dist_info(24), dist_info(25), dist_info(26), dist_info(27), dist_info(28), dist_info(29)};
+
+__device__ __forceinline__ uint16_t e16(uint32_t len, uint32_t kind, uint32_t val) {
+  return (uint16_t)(len | (val << 4) | (kind << 12) | (kind == K_LIT ? 0x8000u : 0u));
+}
+
+// 16-bit entry for symbol `sym` with code length `len`.
+__device__ __forceinline__ uint16_t sym_entry16(int kind, uint32_t len, uint32_t sym) {
+  if (kind == 0) return e16(len, K_LIT, sym);
+  if (kind == 1) {
+    if (sym < 256) return e16(len, K_LIT, sym);
+    if (sym == 256) return e16(len, K_EOB, 0);
+    if (sym <= 285) return e16(len, K_BASE, sym - 257);
+    return e16(len, K_BADSYM, 0);
+  }
+  if (sym < 30) return e16(len, K_BASE, sym);
+  return e16(len, K_BADSYM, 0);
+}
+
+// Full entry (the 32-bit form the exact decoding path works with).
+__device__ __forceinline__ uint32_t expand16(int kind, uint32_t e) {
+  const uint32_t len = e & 15u, val = (e >> 4) & 0xffu;
+  if (e & 0x8000u) return make_ent(len, K_LIT, 0, val);
+  const uint32_t k = (e >> 12) & 7u;
+  if (k == K_BASE) {
+    const uint32_t info = kind == 1 ? kLenInfo[val] : kDistInfo[val];
+    return make_ent(len, K_BASE, info >> 16, info & 0xffffu);
+  }
+  return make_ent(len, k, 0, val);
+}
+
 // Code-length code order, RFC 1951 Sec. 3.2.7.
 static __constant__ uint8_t kClenOrder[19] = {16, 17, 18, 0, 8,  7, 9,  6, 10, 5,
                                        11, 4,  12, 3, 13, 2, 14, 1, 15};
 
 // A canonical code in shared memory.
 struct HCode {
-  uint32_t* table;   // 1 << tb entries
+  uint16_t* table;   // 1 << tb entries (16-bit form)
   uint16_t* sorted;  // symbols by (length, symbol)
   uint16_t* first;   // [16] first code of each length
   uint16_t* count;   // [16] codes of each length
@@ -151,21 +205,21 @@ static __device__ __noinline__ int32_t build_code(HCode& c, const uint8_t* lens,
   const int tb = c.tb;
   for (int e = (int)lane; e < (1 << tb); e += 32) {
     const uint32_t rev = __brev((uint32_t)e) >> (32 - tb);  // code bits MSB first
-    uint32_t ent;
+    uint16_t ent;
     if (kraft == 0) {
-      ent = make_ent(0, K_BADCODE, 0, 0);
+      ent = e16(0, K_BADCODE, 0);
     } else {
-      ent = make_ent(0, K_LONG, 0, 0);
+      ent = e16(0, K_LONG, 0);
       for (int L = 1; L <= tb; L++) {
         const uint32_t cc = rev >> (tb - L);
         const uint32_t k = cc - c.first[L];
         if (k < c.count[L]) {
-          ent = sym_entry(c.kind, (uint32_t)L, c.sorted[c.offset[L] + k]);
+          ent = sym_entry16(c.kind, (uint32_t)L, c.sorted[c.offset[L] + k]);
           break;
         }
         const uint32_t valid = (kraft + (1u << (15 - L)) - 1) >> (15 - L);
         if (cc >= valid) {
-          ent = make_ent((uint32_t)L, K_BADCODE, 0, 0);
+          ent = e16((uint32_t)L, K_BADCODE, 0);
           break;
         }
       }
@@ -196,8 +250,8 @@ struct InflateSmem {
   static_assert(DIST_ENTRIES >= 128, "distance table also holds the 7-bit code-length table");
   // byte offsets within the decoder's scratch area
   static constexpr int OFF_LIT = 0;
-  static constexpr int OFF_DIST = OFF_LIT + 4 * LIT_ENTRIES;
-  static constexpr int OFF_WIN = OFF_DIST + 4 * DIST_ENTRIES;
+  static constexpr int OFF_DIST = OFF_LIT + 2 * LIT_ENTRIES;
+  static constexpr int OFF_WIN = OFF_DIST + 2 * DIST_ENTRIES;
   static constexpr int OFF_LSORT = OFF_WIN + WIN;  // WIN = 0: no shared window
   static constexpr int OFF_DSORT = OFF_LSORT + 2 * 288;
   static constexpr int OFF_META = OFF_DSORT + 2 * 32;  // 7 x u16[16]
@@ -267,8 +321,8 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
   *produced = 0;
   if (n_in64 >= (int64_t)1 << 29 || (STORE && cap64 > 0xffffffffull)) return ST_BAD_SPAN;
   const uint32_t lane = lane_id();
-  uint32_t* lit_tab = reinterpret_cast<uint32_t*>(scratch + SM::OFF_LIT);
-  uint32_t* dist_tab = reinterpret_cast<uint32_t*>(scratch + SM::OFF_DIST);
+  uint16_t* lit_tab = reinterpret_cast<uint16_t*>(scratch + SM::OFF_LIT);
+  uint16_t* dist_tab = reinterpret_cast<uint16_t*>(scratch + SM::OFF_DIST);
   uint8_t* win = scratch + SM::OFF_WIN;
   uint16_t* meta = reinterpret_cast<uint16_t*>(scratch + SM::OFF_META);
   uint8_t* lens = scratch + SM::OFF_LENS;
@@ -424,7 +478,7 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
         bool bad = false;
         while (have < total) {
           if (in.nb < 16 && !in.refill()) return ST_TIMEOUT;
-          const uint32_t e = dist_tab[in.bb & 127];
+          const uint32_t e = expand16(0, dist_tab[in.bb & 127]);
           const uint32_t L = ent_len(e);
           if (L > in.avail()) { st = ST_TRUNCATED; bad = true; break; }
           if (ent_kind(e) != K_LIT) { st = ST_BAD_HUFFMAN; bad = true; break; }
@@ -480,25 +534,26 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
               in.nb |= 56;
             }
             uint32_t e = lit_tab[in.bb & LITMASK];
-            if ((int32_t)e < 0) {  // up to 3 literals (<= 45 bits)
+            if (e & 0x8000u) {  // up to 3 literals (<= 45 bits)
               uint8_t* o = out + wpos;
               int k = 0;
               do {
                 in.consume(e & 15u);
-                if (lane == 0) o[k] = (uint8_t)(e >> 16);
+                if (lane == 0) o[k] = (uint8_t)(e >> 4);
                 e = lit_tab[in.bb & LITMASK];
-              } while ((int32_t)e < 0 && ++k < 3);
-              wpos += (uint32_t)k + ((int32_t)e < 0 ? 0u : 1u);
+              } while ((e & 0x8000u) && ++k < 3);
+              wpos += (uint32_t)k + ((e & 0x8000u) ? 0u : 1u);
               continue;
             }
-            if ((e & 0x70u) != (K_BASE << 4)) break;  // EOB, long or bad code
-            const uint32_t L = e & 15u, x = (e >> 8) & 15u;
+            if ((e >> 12) != K_BASE) break;  // EOB, long or bad code
+            const uint32_t li = kLenInfo[(e >> 4) & 0xffu];
+            const uint32_t L = e & 15u, x = li >> 16;
             const uint32_t ed = dist_tab[(in.bb >> (L + x)) & DISTMASK];
-            if ((ed & 0x70u) != (K_BASE << 4)) break;
-            const uint32_t Ld = ed & 15u, xd = (ed >> 8) & 15u;
-            const uint32_t mlen = ((e >> 16) & 0x7fffu) + ((uint32_t)(in.bb >> L) & ((1u << x) - 1));
-            const uint32_t d = ((ed >> 16) & 0x7fffu) +
-                               ((uint32_t)(in.bb >> (L + x + Ld)) & ((1u << xd) - 1));
+            if ((ed >> 12) != K_BASE) break;
+            const uint32_t di = kDistInfo[(ed >> 4) & 0xffu];
+            const uint32_t Ld = ed & 15u, xd = di >> 16;
+            const uint32_t mlen = (li & 0xffffu) + ((uint32_t)(in.bb >> L) & ((1u << x) - 1));
+            const uint32_t d = (di & 0xffffu) + ((uint32_t)(in.bb >> (L + x + Ld)) & ((1u << xd) - 1));
             if (d > wpos) break;  // the exact path reports BAD_DISTANCE
             in.consume(L + x + Ld + xd);
             uint8_t* o = out + wpos;
@@ -521,7 +576,7 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
         }
         const bool fast = in.inpos + 8 <= n_in && wpos + 258 <= limit;
         if (in.nb < 48 && !in.refill()) return ST_TIMEOUT;
-        uint32_t e = lit_tab[in.bb & LITMASK];
+        uint32_t e = expand16(1, lit_tab[in.bb & LITMASK]);
         if (fast && ent_kind(e) == K_LIT) {  // up to 3 literals per refill (<= 45 bits)
           int k = 0;
           do {
@@ -531,7 +586,7 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
               else win[(oaddr + wpos) & WMASK] = (uint8_t)ent_val(e);
             }
             wpos++;
-            e = lit_tab[in.bb & LITMASK];
+            e = expand16(1, lit_tab[in.bb & LITMASK]);
           } while (ent_kind(e) == K_LIT && ++k < 3);
           maybe_flush();
           continue;
@@ -559,7 +614,7 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
         const uint32_t mlen = ent_val(e) + (uint32_t)(in.bb & ((1u << x) - 1));
         in.consume(x);
         // distance
-        e = dist_tab[in.bb & DISTMASK];
+        e = expand16(2, dist_tab[in.bb & DISTMASK]);
         if (ent_kind(e) == K_LONG) e = decode_long(dist, in.bb);
         L = ent_len(e);
         kind = ent_kind(e);

@@ -3,7 +3,7 @@
 
 namespace codag {
 
-__global__ void __launch_bounds__(kThreads) inflate_kernel(Args a) { inflate_warp_body<true>(a); }
+__global__ void __launch_bounds__(kThreads, 10) inflate_kernel(Args a) { inflate_warp_body<true>(a); }
 __global__ void __launch_bounds__(kThreads) inflate_sizes_kernel(Args a) {
   inflate_warp_body<false>(a);
 }
