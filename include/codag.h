@@ -92,9 +92,11 @@ enum {
  * codag_decompress - decode n_chunks chunks of one format.
  *
  * CODAG Sec. V-C/V-D (warp-level decompression, all lanes decoding) and
- * Sec. V-E/V-F (coalesced on-demand reading and writing): here one warp
- * decodes one chunk, staging its compressed bytes in shared memory with 1-D
- * TMA bulk copies and writing output with coalesced stores.
+ * Sec. V-E/V-F (coalesced on-demand reading and writing): a Deflate chunk is
+ * decoded by one warp; an RLE chunk by one CTA whose warps decode segments of
+ * it after one warp has walked the run headers.  Compressed bytes are staged
+ * in shared memory with 1-D TMA bulk copies; output is written with
+ * coalesced stores.
  *
  * format        one of codag_format.
  * comp, comp_offsets, out, out_offsets: see the layout above (device).
@@ -108,6 +110,47 @@ enum {
 codag_status codag_decompress(int format, const void *comp, const uint64_t *comp_offsets,
                               uint64_t n_chunks, void *out, const uint64_t *out_offsets,
                               cudaStream_t stream);
+
+/*
+ * codag_decompress_host - codag_decompress from HOST memory to HOST memory,
+ * with the copies overlapped with decoding.
+ *
+ * The paper's pipeline (Sec. II-B) reads compressed chunks from storage into
+ * GPU memory, decodes them and hands the output on; this call is that end to
+ * end step for data that starts and ends in host memory.  The chunks are cut
+ * into slices of about 16 MiB of output (fewer, larger slices when the
+ * chunks are too few to keep the GPU busy); slice i's host-to-device copy,
+ * its decode and its device-to-host copy are ordered by events across
+ * internal streams (one for each copy direction and four for decoding), so
+ * copies in both directions overlap the decoding of other slices, and up to
+ * four slices decode at once.
+ *
+ * h_comp        HOST, concatenated compressed chunks (layout of comp above).
+ * h_comp_offsets, h_out_offsets: HOST uint64[n_chunks + 1], read during the
+ *               call; both must be non-decreasing.
+ * h_out         HOST output buffer, written at h_out[h_out_offsets[c] ..].
+ * d_comp        DEVICE buffer of at least h_comp_offsets[n_chunks] bytes,
+ *               16-byte aligned: the compressed bytes are copied to the same
+ *               offsets in it.
+ * d_out         DEVICE buffer of at least h_out_offsets[n_chunks] bytes
+ *               (8-byte aligned for the RLE formats).
+ * h_status      HOST int32[n_chunks] for the per-chunk status, or NULL; the
+ *               status also stays in the workspace (codag_last_chunk_status).
+ * stream        the call is asynchronous with respect to `stream` like
+ *               codag_decompress: work enqueued on it before the call is
+ *               ordered before the copies, and work enqueued after it waits
+ *               for the last read-back.  h_comp, h_out and h_status must stay valid until
+ *               then; they should be page-locked (cudaHostAlloc or
+ *               cudaHostRegister), or the copies do not overlap.
+ * Calls on one device run one after another on the device (they share the
+ * workspace and the copy streams).  Returns as codag_decompress, plus
+ * CODAG_EINVAL when an offsets array decreases or d_comp / d_out is NULL.
+ * The library has no counterpart in the paper for the slicing itself.
+ */
+codag_status codag_decompress_host(int format, const void *h_comp, const uint64_t *h_comp_offsets,
+                                   uint64_t n_chunks, void *h_out, const uint64_t *h_out_offsets,
+                                   void *d_comp, void *d_out, int32_t *h_status,
+                                   cudaStream_t stream);
 
 /*
  * codag_decompressed_sizes - decoded size in bytes of each chunk.

@@ -55,6 +55,7 @@ def lib() -> ctypes.CDLL:
         vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
         L.codag_decompress.argtypes = [i32, vp, vp, u64, vp, vp, vp]
         L.codag_decompressed_sizes.argtypes = [i32, vp, vp, u64, vp, vp]
+        L.codag_decompress_host.argtypes = [i32, vp, vp, u64, vp, vp, vp, vp, vp, vp]
         L.codag_decompress_batch.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
         L.codag_last_chunk_status.argtypes = [vp, u64, vp]
         L.codag_decompress_batch_noalloc.argtypes = [vp, vp, vp, u64, vp, vp, vp, vp]
@@ -68,6 +69,7 @@ def lib() -> ctypes.CDLL:
         L.codag_set_parts_per_chunk.argtypes = [i32]
         L.codag_get_parts_per_chunk.restype = i32
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
+                     "codag_decompress_host",
                      "codag_last_chunk_status", "codag_batch_graph_create",
                      "codag_batch_graph_launch", "codag_batch_graph_destroy",
                      "codag_set_batch_ctas_per_sm", "codag_decompress_batch_noalloc",
@@ -86,7 +88,9 @@ def _ptr(x) -> int | None:
         return None
     if isinstance(x, int):
         return x
-    return x.data_ptr()
+    if hasattr(x, "data_ptr"):  # torch tensor (device or host)
+        return x.data_ptr()
+    return x.ctypes.data  # numpy array (host)
 
 
 def _stream(s) -> int | None:
@@ -111,6 +115,17 @@ def codag_decompress(fmt, comp, comp_offsets, n_chunks: int, out, out_offsets, s
     """Decode n_chunks chunks of one format (device tensors or raw pointers)."""
     _check(lib().codag_decompress(_fmt(fmt), _ptr(comp), _ptr(comp_offsets), n_chunks, _ptr(out),
                                   _ptr(out_offsets), _stream(stream)), "codag_decompress")
+
+
+def codag_decompress_host(fmt, h_comp, h_comp_offsets, n_chunks: int, h_out, h_out_offsets,
+                          d_comp, d_out, h_status=None, stream=None):
+    """Host-to-host decode with the copies overlapped with decoding.  h_*:
+    host arrays (numpy, or page-locked torch CPU tensors for overlap);
+    d_comp / d_out: device buffers as large as the compressed and decoded
+    data.  Asynchronous on `stream`."""
+    _check(lib().codag_decompress_host(_fmt(fmt), _ptr(h_comp), _ptr(h_comp_offsets), n_chunks,
+                                       _ptr(h_out), _ptr(h_out_offsets), _ptr(d_comp), _ptr(d_out),
+                                       _ptr(h_status), _stream(stream)), "codag_decompress_host")
 
 
 def codag_decompressed_sizes(fmt, comp, comp_offsets, n_chunks: int, sizes_out, stream=None):

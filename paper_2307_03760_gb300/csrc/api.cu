@@ -5,6 +5,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/codag.h"
 #include "kernels.cuh"
@@ -29,7 +30,24 @@ codag_status cuda_fail(cudaError_t e, const char* what) {
 
 constexpr int kMaxDevices = 64;
 
+// Host-to-host decode (codag_decompress_host): two copy streams, kPipeDecode
+// decode streams (slices decode concurrently, so that small slices still fill
+// the GPU), events per slice, and device copies of the two offsets arrays.
+constexpr uint64_t kSliceBytes = 16ull << 20;
+constexpr int kMaxSlices = 64;
+constexpr int kPipeDecode = 4;
+struct HostPipe {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaStream_t dec[kPipeDecode] = {};
+  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t copied[kMaxSlices] = {}, decoded[kMaxSlices] = {};
+  bool used = false;         // `done` marks the end of an earlier call
+  uint64_t* offs = nullptr;  // comp offsets, then out offsets
+  uint64_t offs_cap = 0;     // words
+};
+
 struct Workspace {
+  HostPipe pipe;
   int32_t* status = nullptr;     // per-chunk status of the last plain call
   uint64_t status_cap = 0;
   uint64_t last_n = 0;
@@ -120,6 +138,11 @@ codag_status check_common(const void* comp, const uint64_t* comp_offsets, uint64
   return CODAG_OK;
 }
 
+codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
+                           const uint64_t* comp_offsets, uint64_t n, void* out,
+                           const uint64_t* out_offsets, uint64_t* sizes, bool store,
+                           int32_t* status, cudaStream_t stream);
+
 codag_status launch_plain(int format, const void* comp, const uint64_t* comp_offsets, uint64_t n,
                           void* out, const uint64_t* out_offsets, uint64_t* sizes, bool store,
                           cudaStream_t stream) {
@@ -140,6 +163,18 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   if ((s = current_ws(&w)) != CODAG_OK) return s;
   if ((s = grow_status(*w, n)) != CODAG_OK) return s;
   w->last_n = n;
+  return launch_kernel(*w, format, comp, comp_offsets, n, out, out_offsets, sizes, store, w->status,
+                       stream);
+}
+
+// One plain decode (or sizes) launch over chunks [0, n) of the given arrays,
+// statuses to `status`.  Arguments are checked and g_mu is held by the caller.
+codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
+                           const uint64_t* comp_offsets, uint64_t n, void* out,
+                           const uint64_t* out_offsets, uint64_t* sizes, bool store,
+                           int32_t* status, cudaStream_t stream) {
+  const Workspace* w = &ws;
+  const int fam = family_of(format);
   Args a{};
   a.comp = static_cast<const uint8_t*>(comp);
   a.comp_off = comp_offsets;
@@ -147,7 +182,7 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   a.out = static_cast<uint8_t*>(out);
   a.out_off = out_offsets;
   a.sizes = sizes;
-  a.status = w->status;
+  a.status = status;
   a.format = format;
   const void* fn;
   unsigned grid, block;
@@ -171,6 +206,7 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
     if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;  // ring fallback fits
     a.stage_bytes = stage;
     smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
+    if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);
     if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
     else fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
   }
@@ -179,6 +215,63 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   if (e != cudaSuccess) return cuda_fail(e, "decode launch");
   g_launches.fetch_add(1);
   return CODAG_OK;
+}
+
+codag_status init_pipe(HostPipe& p) {
+  if (p.h2d) return CODAG_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&p.h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p.d2h, cudaStreamNonBlocking);
+  for (int i = 0; i < kPipeDecode && e == cudaSuccess; i++)
+    e = cudaStreamCreateWithFlags(&p.dec[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
+  for (int i = 0; i < kMaxSlices && e == cudaSuccess; i++) {
+    e = cudaEventCreateWithFlags(&p.copied[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.decoded[i], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    p.h2d = nullptr;  // retried on the next call; the objects made so far are kept alive
+    return cuda_fail(e, "copy stream / event creation");
+  }
+  return CODAG_OK;
+}
+
+codag_status grow_offs(HostPipe& p, uint64_t words) {
+  if (words <= p.offs_cap) return CODAG_OK;
+  if (p.offs) cudaFree(p.offs);
+  p.offs = nullptr;
+  p.offs_cap = 0;
+  const uint64_t cap = words < 2048 ? 2048 : words + words / 4;
+  if (cudaMalloc(&p.offs, cap * sizeof(uint64_t)) != cudaSuccess)
+    return fail(CODAG_ENOMEM, "offsets workspace allocation failed");
+  p.offs_cap = cap;
+  return CODAG_OK;
+}
+
+// Slice boundaries (chunk indices, first 0, last n): about kSliceBytes of
+// output each, but at least min_chunks chunks (enough decoders for
+// kPipeDecode concurrent slices to fill the GPU), at most kMaxSlices, no
+// empty slice.
+std::vector<uint64_t> plan_slices(const uint64_t* out_offsets, uint64_t n, uint64_t min_chunks) {
+  const uint64_t o0 = out_offsets[0], total = out_offsets[n] - o0;
+  uint64_t S = (total + kSliceBytes - 1) / kSliceBytes;
+  if (min_chunks && S > n / min_chunks) S = n / min_chunks;
+  if (S > (uint64_t)kMaxSlices) S = kMaxSlices;
+  if (S > n) S = n;
+  if (S < 1) S = 1;
+  std::vector<uint64_t> b{0};
+  for (uint64_t s = 1; s < S; s++) {
+    const uint64_t target = o0 + (total / S) * s;
+    uint64_t lo = b.back() + 1, hi = n;  // first c in [lo, n) with out_offsets[c] >= target
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (out_offsets[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo < n) b.push_back(lo);
+  }
+  b.push_back(n);
+  return b;
 }
 
 // Enqueue the batch path with the given scratch (status, order, keys, counters).
@@ -258,6 +351,84 @@ codag_status codag_decompressed_sizes(int format, const void* comp, const uint64
                                       uint64_t n_chunks, uint64_t* sizes_out, cudaStream_t stream) {
   return launch_plain(format, comp, comp_offsets, n_chunks, nullptr, nullptr, sizes_out, false,
                       stream);
+}
+
+codag_status codag_decompress_host(int format, const void* h_comp, const uint64_t* h_comp_offsets,
+                                   uint64_t n, void* h_out, const uint64_t* h_out_offsets,
+                                   void* d_comp, void* d_out, int32_t* h_status,
+                                   cudaStream_t stream) {
+  if (!family_of(format)) return fail(CODAG_EINVAL, "unknown format");
+  if (n == 0) return CODAG_OK;
+  if (!h_comp || !h_comp_offsets || !h_out || !h_out_offsets || !d_comp || !d_out)
+    return fail(CODAG_EINVAL, "codag_decompress_host: NULL pointer");
+  codag_status s = check_common(d_comp, h_comp_offsets, n);
+  if (s != CODAG_OK) return s;
+  if (is_rle(format) && (reinterpret_cast<uintptr_t>(d_out) & 7))
+    return fail(CODAG_EINVAL, "RLE out must be 8-byte aligned");
+  for (uint64_t c = 0; c < n; c++)
+    if (h_comp_offsets[c + 1] < h_comp_offsets[c] || h_out_offsets[c + 1] < h_out_offsets[c])
+      return fail(CODAG_EINVAL, "codag_decompress_host: offsets must be non-decreasing");
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  if ((s = current_ws(&w)) != CODAG_OK) return s;
+  if ((s = grow_status(*w, n)) != CODAG_OK) return s;
+  HostPipe& p = w->pipe;
+  if ((s = init_pipe(p)) != CODAG_OK) return s;
+  if ((s = grow_offs(p, 2 * (n + 1))) != CODAG_OK) return s;
+  w->last_n = n;
+  // a Deflate decoder is one warp (about 40 resident per SM), an RLE decoder
+  // a CTA (a few per SM)
+  const uint64_t min_chunks =
+      (uint64_t)w->sm_count * (family_of(format) == 3 ? 40 : 8) / kPipeDecode;
+  const std::vector<uint64_t> bounds = plan_slices(h_out_offsets, n, min_chunks);
+  uint64_t* d_coff = p.offs;
+  uint64_t* d_ooff = p.offs + (n + 1);
+  const uint8_t* hc = static_cast<const uint8_t*>(h_comp);
+  uint8_t* dc = static_cast<uint8_t*>(d_comp);
+  uint8_t* ho = static_cast<uint8_t*>(h_out);
+  uint8_t* dd = static_cast<uint8_t*>(d_out);
+
+  // order: earlier work on `stream` and an earlier host call (which shares
+  // the offsets copy and the statuses) before the first copy
+  cudaError_t e = cudaEventRecord(p.start, stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.h2d, p.start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p.d2h, p.start, 0);
+  if (e == cudaSuccess && p.used) e = cudaStreamWaitEvent(p.h2d, p.done, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_coff, h_comp_offsets, (n + 1) * 8, cudaMemcpyHostToDevice, p.h2d);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_ooff, h_out_offsets, (n + 1) * 8, cudaMemcpyHostToDevice, p.h2d);
+  if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host setup");
+  // A slice's kernels read its chunks' bytes and, for the 16-byte alignment
+  // of a staged copy, up to 15 bytes before the first chunk: those belong to
+  // the previous slice, whose copy is earlier on the same stream.
+  uint64_t copied_to = h_comp_offsets[0];
+  for (size_t k = 0; k + 1 < bounds.size(); k++) {
+    const uint64_t a = bounds[k], b = bounds[k + 1];
+    const uint64_t hi = h_comp_offsets[b];
+    if (hi > copied_to)
+      e = cudaMemcpyAsync(dc + copied_to, hc + copied_to, hi - copied_to, cudaMemcpyHostToDevice, p.h2d);
+    copied_to = hi > copied_to ? hi : copied_to;
+    cudaStream_t ds = p.dec[k % kPipeDecode];
+    if (e == cudaSuccess) e = cudaEventRecord(p.copied[k], p.h2d);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, p.copied[k], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy in");
+    s = launch_kernel(*w, format, d_comp, d_coff + a, b - a, d_out, d_ooff + a, nullptr, true,
+                      w->status + a, ds);
+    if (s != CODAG_OK) return s;
+    e = cudaEventRecord(p.decoded[k], ds);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.d2h, p.decoded[k], 0);
+    const uint64_t ob = h_out_offsets[a], oe = h_out_offsets[b];
+    if (e == cudaSuccess && oe > ob)
+      e = cudaMemcpyAsync(ho + ob, dd + ob, oe - ob, cudaMemcpyDeviceToHost, p.d2h);
+    if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy out");
+  }
+  if (h_status) e = cudaMemcpyAsync(h_status, w->status, n * 4, cudaMemcpyDeviceToHost, p.d2h);
+  if (e == cudaSuccess) e = cudaEventRecord(p.done, p.d2h);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, p.done, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host finish");
+  p.used = true;
+  return CODAG_OK;
 }
 
 codag_status codag_decompress_batch(const uint8_t* formats, const void* comp,

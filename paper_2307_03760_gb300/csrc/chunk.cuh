@@ -59,14 +59,16 @@ __device__ __forceinline__ uint64_t part_target(uint64_t cap_v, uint32_t k, uint
 template <int FAMILY, bool STORE, class In>
 __device__ __forceinline__ PartResult decode_rle_part(In& in, uint8_t* scratch, const Args& a,
                                                       const ChunkGeom& g, int format, int64_t base,
-                                                      uint64_t count0, uint64_t hi) {
+                                                      uint64_t count0, uint64_t hi,
+                                                      V1Bitmap vb = V1Bitmap{nullptr, 0, 0}) {
   OffsetIn<In> sub{&in, base};
   uint64_t* out = reinterpret_cast<uint64_t*>(a.out + g.os);
   const uint64_t cap_v = g.cap / 8;
   PartResult r;
+  vb.off += (uint32_t)base;
   if (FAMILY == 1)
     r = rle_v1_part<STORE>(sub, reinterpret_cast<uint16_t*>(scratch), g.n_in - base,
-                           format == FMT_RLE_V1_I64, out, cap_v, count0, hi);
+                           format == FMT_RLE_V1_I64, out, cap_v, count0, hi, vb);
   else
     r = rle_v2_part<STORE>(sub, scratch, g.n_in - base, format == FMT_RLE_V2_I64, out, cap_v,
                            count0, hi);
@@ -131,7 +133,8 @@ __device__ __forceinline__ bool wait_published(volatile uint32_t* published, uin
 }
 
 // Plain RLE kernels: one CTA per chunk, K warps.  Shared memory:
-// [stage][K scratch][mbarrier][key][published][claimed][segment tables].
+// [stage][K scratch][mbarrier][key][published][claimed][segment tables]
+// [RLE v1: terminator bitmap of the stage].
 //
 // A chunk that fits the stage is copied in whole by TMA (warp 0, one
 // mbarrier).  Its output is cut into nseg segments of about equal numbers of
@@ -158,6 +161,7 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   int64_t* split_pos = reinterpret_cast<int64_t*>(bar + 3);      // [kMaxSeg + 1]
   uint64_t* split_cnt = reinterpret_cast<uint64_t*>(split_pos + kMaxSeg + 1);
   uint64_t* target = split_cnt + kMaxSeg + 1;
+  uint32_t* bitmap = reinterpret_cast<uint32_t*>(smem + stage_bytes + K * kRleScratch + kRleCtaExtra);
   const ChunkGeom g = chunk_geom<FAMILY, STORE>(a, c);
   if (g.bad != ST_OK) {
     if (threadIdx.x == 0) {
@@ -210,15 +214,25 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     }
     bool ok = mbar_wait_bounded(bar, 0);
     if (!ok) ok = mbar_wait_bounded(bar, 0);  // second bounded wait for the copies in flight
-    __syncthreads();  // also publishes warp 0's tail bytes
+    ok = __syncthreads_and(ok);  // CTA-uniform; also publishes warp 0's tail bytes
     StagedInput in{stage, gsrc, skew};
+    V1Bitmap vb{nullptr, (uint32_t)skew, 0};
+    if (FAMILY == 1 && ok) {
+      uint32_t* rank = bitmap + rle_v1_bitmap_words(stage_bytes);
+      v1_build_bitmap(stage, (uint32_t)skew, (uint32_t)g.n_in, bitmap, rank,
+                      rank + rle_v1_bitmap_words(stage_bytes));
+      vb.bm = bitmap;
+      vb.last_word = ((uint32_t)skew + (uint32_t)g.n_in + 31) >> 5;
+      __syncthreads();
+    }
     if (!ok) {
       if (threadIdx.x == 0) *key = status_key(PartResult{ST_TIMEOUT, 0, 0});
     } else {
       if (warp == 0 && nseg > 1) {
         if (FAMILY == 1)
-          rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)nseg - 1,
-                      split_pos, split_cnt, published);
+          rle_v1_walk_staged(in, bitmap, bitmap + rle_v1_bitmap_words(stage_bytes),
+                             (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
+                             published);
         else
           rle_v2_walk(in, g.n_in, target, (int)nseg - 1, split_pos, split_cnt, published);
       }
@@ -234,7 +248,7 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
           __threadfence_block();
           const uint64_t hi = k + 1 < nseg ? target[k + 1] : ~0ull;
           r = decode_rle_part<FAMILY, STORE>(in, scratch, a, g, a.format, split_pos[k],
-                                             split_cnt[k], hi);
+                                             split_cnt[k], hi, vb);
         }
         if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
         if (!STORE && k + 1 == nseg && lane_id() == 0) a.sizes[c] = r.count;

@@ -42,7 +42,13 @@ constexpr int kSegValues = 1024;
 // per-CTA extras: mbarrier, status key, published/claimed, split positions,
 // counts and targets
 constexpr int kRleCtaExtra = 24 + 3 * (kMaxSeg + 1) * 8;
-constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra;
+// RLE v1 staged chunks add, after the extra region, a terminator bitmap of
+// the stage and its rank directory (one word per 32 stage bytes plus 32 words
+// of read slack each) and one word per warp for the rank totals.
+__host__ __device__ constexpr int rle_v1_bitmap_words(int stage_bytes) { return stage_bytes / 32 + 32; }
+__host__ __device__ constexpr int rle_v1_bitmap_bytes(int stage_bytes) { return (2 * rle_v1_bitmap_words(stage_bytes) + 32) * 4; }
+constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra +
+                            rle_v1_bitmap_bytes(16 * RleRing::SMEM);
 constexpr int kBatchWarp =
     round128(RleRing::SMEM + cmax(DeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
 

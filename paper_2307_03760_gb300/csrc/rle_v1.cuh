@@ -11,6 +11,9 @@
 //     tests 4 bytes of a 128-byte window for the stop bit, __ballot_sync
 //     gives a 128-bit terminator map, __popc ranks every terminator, and the
 //     ranked end offsets go to shared memory; lane j then decodes varint j;
+//   - when the chunk is staged whole, the CTA first builds a terminator
+//     bitmap of it, so that skipping or splitting a literal group is a
+//     rank/select over 32 words (1 KiB of stream) per warp step;
 //   - runs are written by all lanes, value i = base + i*delta (the paper's
 //     write_run primitive, Table 2), as coalesced 8-byte stores.
 // Status order matches the oracle: header/varint problems in stream order
@@ -23,6 +26,69 @@ namespace codag {
 
 // shared scratch beyond the ring: u16 end offsets of up to 128 varints
 constexpr int kRleV1Scratch = 128 * 2;
+
+// Terminator bitmap of a chunk staged whole in shared memory: bit i of word t
+// is set when stage byte 32t + i is a chunk byte below 0x80 (the last byte of
+// a varint, or a header or delta byte).  With it, the k-th varint end after a
+// position is a rank/select query instead of a byte scan.  A rank directory
+// beside it holds, for every word, the set bits in all earlier words.
+struct V1Bitmap {
+  const uint32_t* bm;  // shared; nullptr: no bitmap (ring input)
+  uint32_t off;        // stage position of position 0 of the input view
+  uint32_t last_word;  // words from last_word on are zero (32 more are readable)
+};
+
+// Bitmap words a CTA builds for a chunk ending at stage position `end`.
+__host__ __device__ __forceinline__ uint32_t v1_bitmap_words(uint32_t end) { return (end + 31) / 32 + 32; }
+
+// Built by every warp of the CTA: warp w takes a block of words, one ballot
+// per word, then ranks them with a warp scan; the block offsets come from the
+// other warps' totals (`tot`: one shared word per warp).  Contains a CTA
+// barrier; the caller synchronises the CTA again before use.
+__device__ __forceinline__ void v1_build_bitmap(const uint8_t* stage, uint32_t skew, uint32_t n_in,
+                                                uint32_t* bm, uint32_t* rk, uint32_t* tot) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t end = skew + n_in;
+  const uint32_t words = v1_bitmap_words(end);
+  const uint32_t per = ((words + nw - 1) / nw + 31) & ~31u;
+  const uint32_t t_lo = warp * per;
+  const uint32_t t_hi = t_lo + per < words ? t_lo + per : words;
+  uint32_t run = 0;
+  for (uint32_t t0 = t_lo; t0 < t_hi; t0 += 32) {
+    uint32_t mine = 0;
+    for (uint32_t k = 0; k < 32; k++) {
+      const uint32_t p = 32 * (t0 + k) + lane;
+      const uint32_t b = __ballot_sync(FULL, p >= skew && p < end && stage[p] < 0x80);
+      if (lane == k) mine = b;
+    }
+    const uint32_t c = __popc(mine);
+    const uint32_t incl = warp_incl_scan32(c);
+    if (t0 + lane < t_hi) {
+      bm[t0 + lane] = mine;
+      rk[t0 + lane] = run + incl - c;
+    }
+    run += __shfl_sync(FULL, incl, 31);
+  }
+  if (lane == 0) tot[warp] = run;
+  __syncthreads();
+  uint32_t off = 0;
+  for (uint32_t v = 0; v < warp; v++) off += tot[v];
+  for (uint32_t t = t_lo + lane; t < t_hi; t += 32) rk[t] += off;
+}
+
+// Position (0..31) of the r-th set bit (r >= 1) of w, which has >= r set bits.
+__device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t r) {
+  uint32_t pos = 0, c;
+  c = __popc(w & 0xffffu);
+  if (r > c) { r -= c; w >>= 16; pos += 16; }
+  c = __popc(w & 0xffu);
+  if (r > c) { r -= c; w >>= 8; pos += 8; }
+  c = __popc(w & 0xfu);
+  if (r > c) { r -= c; w >>= 4; pos += 4; }
+  c = __popc(w & 0x3u);
+  if (r > c) { r -= c; w >>= 2; pos += 2; }
+  return pos + ((r > (w & 1u)) ? 1u : 0u);
+}
 
 // Decode the low 7-bit groups of an 8-byte window (byte k -> bits 7k..7k+6).
 __device__ __forceinline__ uint64_t varint_compact8(uint64_t x) {
@@ -74,7 +140,7 @@ struct V1Group {
 
 template <class In>
 __device__ __forceinline__ int32_t v1_parse_group(In& in, int64_t pos, int64_t n_in, uint16_t* ends,
-                                                  V1Group& gr) {
+                                                  V1Group& gr, const V1Bitmap& vb = V1Bitmap{nullptr, 0, 0}) {
   const uint32_t lane = lane_id();
   const uint64_t w = in.u64(pos);
   const int h = (int8_t)(w & 0xff);
@@ -93,6 +159,47 @@ __device__ __forceinline__ int32_t v1_parse_group(In& in, int64_t pos, int64_t n
   gr.len = (uint32_t)cnt;
   const int64_t g = pos + 1;  // first varint byte
   gr.g = g;
+  if (vb.bm) {
+    // Fast path: the cnt varint ends from one window of 32 bitmap words
+    // (1 KiB).  Lane j finds the word holding rank j by a binary search over
+    // the warp's prefix counts, then the bit within it.  Groups that do not
+    // end inside the window, or hold a varint longer than 10 bytes, take the
+    // exact byte scan below, which also decides their status.
+    const uint32_t sp = vb.off + (uint32_t)g;
+    const uint32_t w0 = sp >> 5;
+    uint32_t word = vb.bm[w0 + lane];
+    if (lane == 0) word &= ~0u << (sp & 31);
+    const uint32_t c = __popc(word);
+    const uint32_t S = warp_incl_scan32(c);
+    if (__shfl_sync(FULL, S, 31) >= (uint32_t)cnt) {
+      const uint32_t excl = S - c;
+      bool bad = false;
+      uint32_t prev_end = sp - 1;
+      for (uint32_t j0 = 0; j0 < (uint32_t)cnt; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        uint32_t k = 0;
+#pragma unroll
+        for (uint32_t step = 16; step; step >>= 1)
+          if (__shfl_sync(FULL, S, k + step - 1) <= j) k += step;
+        const uint32_t wk = __shfl_sync(FULL, word, k);
+        const uint32_t ek = __shfl_sync(FULL, excl, k);
+        const uint32_t e = (w0 + k) * 32 + select_bit(wk, j - ek + 1);
+        uint32_t prv = __shfl_up_sync(FULL, e, 1);
+        if (lane == 0) prv = prev_end;
+        if (j < (uint32_t)cnt) {
+          ends[j] = (uint16_t)(e - sp);
+          bad |= e - prv > 10;
+        }
+        prev_end = __shfl_sync(FULL, e, 31);
+      }
+      if (!__any_sync(FULL, bad)) {
+        __syncwarp();
+        gr.end = g + ends[cnt - 1] + 1;
+        return ST_OK;
+      }
+      __syncwarp();
+    }
+  }
   const int64_t avail = n_in - g;
   const int64_t span = avail < 1280 + 128 ? avail : 1280 + 128;
   if (span > 0 && !in.ensure(g, g + span)) return ST_TIMEOUT;
@@ -186,11 +293,131 @@ __device__ __forceinline__ void rle_v1_walk(In& in, uint16_t* ends, int64_t n_in
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
+// Walk of a staged chunk (one warp) with its terminator bitmap and rank
+// directory: same contract as rle_v1_walk, but a literal group is skipped in
+// one step: its end is the (rank + cnt)-th set bit, whose word is the first
+// with a directory entry that reaches that rank (one ballot over 32 words).
+// The walk is lenient: it does not check varint lengths, and it stops at a
+// group it cannot skip (the remaining splits get that position).  This is
+// safe because a malformed stream decodes exactly like a well-formed one up
+// to its first error: every group before it is skipped exactly, so the part
+// containing the first error starts at or before it and reports it, and
+// every later part starts after it, so the first error in stream order still
+// wins when the part statuses are combined.
+__device__ __forceinline__ void rle_v1_walk_staged(const StagedInput& in, const uint32_t* bm,
+                                                   const uint32_t* rk, uint32_t n_in,
+                                                   const uint64_t* target, int nsplit,
+                                                   int64_t* split_pos, uint64_t* split_cnt,
+                                                   volatile uint32_t* published) {
+  const uint32_t lane = lane_id();
+  const uint32_t skew = (uint32_t)in.skew;
+  const uint32_t last_word = (skew + n_in + 31) >> 5;
+  uint32_t pos = 0;
+  uint64_t count = 0;
+  int k = 1;
+  uint64_t tk = target[1];
+  while (pos < n_in) {
+    if (count >= tk) {
+      do {
+        publish_split(k, pos, count, split_pos, split_cnt, published);
+        if (++k > nsplit) return;
+        tk = target[k];
+      } while (count >= tk);
+    }
+    const int h = (int8_t)in.byte(pos);
+    if (h >= 0) {  // run: header, delta byte, base varint
+      if (pos + 2 >= n_in) break;
+      uint64_t v;
+      int vlen;
+      if (varint_at(in, pos + 2, (int64_t)n_in - (pos + 2), &v, &vlen) != ST_OK) break;
+      pos += 2 + (uint32_t)vlen;
+      count += (uint32_t)h + 3;
+    } else {  // literal group: the end of its -h-th varint
+      const uint32_t sp = pos + 1 + skew;
+      const uint32_t w0 = sp >> 5;
+      const uint32_t T = rk[w0] + __popc(bm[w0] & ((1u << (sp & 31)) - 1u)) + (uint32_t)(-h);
+      bool found = false;
+      for (uint32_t wb = w0; wb < last_word; wb += 32) {
+        const uint32_t t = wb + lane;
+        const uint32_t hit = __ballot_sync(FULL, rk[t + 1] >= T);
+        if (hit) {
+          const uint32_t bit = select_bit(bm[t], T - rk[t]);  // meaningful in lane L only
+          const int L = __ffs(hit) - 1;
+          pos = (wb + (uint32_t)L) * 32 + __shfl_sync(FULL, bit, L) - skew + 1;
+          found = true;
+          break;
+        }
+      }
+      if (!found) break;
+      count += (uint32_t)(-h);
+    }
+  }
+  for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+}
+
+// Decode a literal group of cnt varints whose first byte is at view position
+// g straight from the terminator bitmap: lane j finds the end of varint j
+// (binary search over the warp's prefix counts, then the bit in the word),
+// the previous lane's end gives its start, and the value is decoded and
+// stored in the same step.  Returns false, having stored at most part of the
+// group, when the group does not end within one 32-word window or holds a
+// varint longer than 10 bytes; the caller then takes the exact path, which
+// decides the status.  On success *end is the view position after the group.
+template <class In>
+__device__ __forceinline__ bool v1_literal_direct(const In& in, const V1Bitmap& vb, uint32_t g,
+                                                  uint32_t cnt, bool is_signed,
+                                                  uint64_t* __restrict__ o, int64_t* end) {
+  const uint32_t lane = lane_id();
+  const uint32_t sp = vb.off + g;
+  const uint32_t w0 = sp >> 5;
+  uint32_t word = vb.bm[w0 + lane];
+  if (lane == 0) word &= ~0u << (sp & 31);
+  const uint32_t c = __popc(word);
+  const uint32_t S = warp_incl_scan32(c);
+  if (__shfl_sync(FULL, S, 31) < cnt) return false;
+  const uint32_t excl = S - c;
+  bool bad = false;
+  uint32_t prev_end = sp - 1, e = 0;
+  for (uint32_t j0 = 0; j0 < cnt; j0 += 32) {
+    const uint32_t j = j0 + lane;
+    uint32_t k = 0;
+#pragma unroll
+    for (uint32_t step = 16; step; step >>= 1)
+      if (__shfl_sync(FULL, S, k + step - 1) <= j) k += step;
+    const uint32_t wk = __shfl_sync(FULL, word, k);
+    const uint32_t ek = __shfl_sync(FULL, excl, k);
+    e = (w0 + k) * 32 + select_bit(wk, j - ek + 1);
+    uint32_t prv = __shfl_up_sync(FULL, e, 1);
+    if (lane == 0) prv = prev_end;
+    const uint32_t len = e - prv;
+    if (j < cnt) {
+      bad |= len > 10;
+      if (len <= 10) {
+        const int64_t s0 = (int64_t)(prv + 1 - vb.off);
+        const uint64_t x = in.u64(s0);
+        uint64_t v;
+        if (len <= 8) {
+          v = varint_compact8(x & lowmask64(8 * len));
+        } else {
+          const uint64_t y = in.u64(s0 + 8);
+          v = varint_compact8(x) | ((y & 0x7full) << 56);
+          if (len == 10) v |= ((y >> 8) & 0x1ull) << 63;
+        }
+        o[j] = is_signed ? unzigzag(v) : v;
+      }
+    }
+    prev_end = __shfl_sync(FULL, e, 31);
+  }
+  if (__any_sync(FULL, bad)) return false;
+  *end = (int64_t)__shfl_sync(FULL, e, (int)((cnt - 1) & 31)) - (int64_t)vb.off + 1;
+  return true;
+}
+
 // Decode part of one RLE v1 chunk; same contract as rle_v2_part.
 template <bool STORE, class In>
 __device__ PartResult rle_v1_part(In& in, uint16_t* ends, int64_t n_in, bool is_signed,
                                   uint64_t* __restrict__ out, uint64_t cap_values, uint64_t count0,
-                                  uint64_t hi_v) {
+                                  uint64_t hi_v, const V1Bitmap& vb = V1Bitmap{nullptr, 0, 0}) {
   const uint32_t lane = lane_id();
   const bool last = hi_v == ~0ull;
   int64_t pos = 0;
@@ -198,8 +425,20 @@ __device__ PartResult rle_v1_part(In& in, uint16_t* ends, int64_t n_in, bool is_
   while (pos < n_in) {
     if (count >= hi_v) return PartResult{ST_OK, -1, count};
     if (!in.ensure(pos, pos + 24)) return part_error(ST_TIMEOUT, 0, count);
+    if (STORE && vb.bm) {  // staged chunk: literal groups straight from the bitmap
+      const int h = (int8_t)in.byte(pos);
+      if (h < 0 && count <= cap_values && (uint64_t)(-h) <= cap_values - count) {
+        int64_t end;
+        if (v1_literal_direct(in, vb, (uint32_t)pos + 1, (uint32_t)(-h), is_signed, out + count,
+                              &end)) {
+          count += (uint32_t)(-h);
+          pos = end;
+          continue;
+        }
+      }
+    }
     V1Group gr;
-    const int32_t st = v1_parse_group(in, pos, n_in, ends, gr);
+    const int32_t st = v1_parse_group(in, pos, n_in, ends, gr, vb);
     if (st != ST_OK) return part_error(st, st == ST_TIMEOUT ? 0 : pos, count);
     if (count > cap_values || gr.len > cap_values - count) return part_error(ST_OVERFLOW, pos, count);
     if (STORE) {

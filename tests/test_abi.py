@@ -61,6 +61,28 @@ def test_argument_errors_without_gpu():
     assert L.codag_batch_graph_launch(None, None) == codag.CODAG_EINVAL
 
 
+def test_host_entry_argument_errors_without_gpu():
+    import numpy as np
+    L = codag.lib()
+    h = np.zeros(64, np.uint8)
+    off = np.array([0, 8, 16], np.uint64)
+    dec = np.array([0, 16, 8], np.uint64)  # decreasing
+    P = lambda a: a.ctypes.data
+    # unknown format, zero chunks
+    assert L.codag_decompress_host(42, P(h), P(off), 2, P(h), P(off), 0x1000, 0x2000, None, None) == codag.CODAG_EINVAL
+    assert L.codag_decompress_host(1, None, None, 0, None, None, None, None, None, None) == codag.CODAG_OK
+    # NULL host or device buffers
+    assert L.codag_decompress_host(1, None, P(off), 2, P(h), P(off), 0x1000, 0x2000, None, None) == codag.CODAG_EINVAL
+    assert L.codag_decompress_host(1, P(h), P(off), 2, P(h), P(off), None, 0x2000, None, None) == codag.CODAG_EINVAL
+    # misaligned device buffers (never dereferenced)
+    assert L.codag_decompress_host(3, P(h), P(off), 2, P(h), P(off), 0x1008, 0x2000, None, None) == codag.CODAG_EINVAL
+    assert L.codag_decompress_host(2, P(h), P(off), 2, P(h), P(off), 0x1000, 0x2004, None, None) == codag.CODAG_EINVAL
+    # decreasing offsets, compressed or decoded
+    assert L.codag_decompress_host(2, P(h), P(dec), 2, P(h), P(off), 0x1000, 0x2000, None, None) == codag.CODAG_EINVAL
+    assert L.codag_decompress_host(2, P(h), P(off), 2, P(h), P(dec), 0x1000, 0x2000, None, None) == codag.CODAG_EINVAL
+    assert b"non-decreasing" in L.codag_last_error()
+
+
 def test_python_binding_names_match_abi():
     for name in declared_functions():
         if name in ("codag_last_error",):
