@@ -234,7 +234,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
                              (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
                              published);
         else
-          rle_v2_walk(in, g.n_in, target, (int)nseg - 1, split_pos, split_cnt, published);
+          rle_v2_walk_staged(in, (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
+                             published);
       }
       for (;;) {
         uint32_t k = 0;

@@ -155,6 +155,81 @@ __device__ __forceinline__ void rle_v2_walk(In& in, int64_t n_in, const uint64_t
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
+// Extent of the run at pos for the staged walk: its value count and end,
+// from the header bytes alone, without the field checks of v2_parse_run
+// (lenient, like rle_v1_walk_staged: exact on well-formed runs, and the part
+// decoders check every run).  Returns false where it cannot tell (a DELTA
+// varint that is malformed or runs past the chunk); the caller stops there.
+template <class In>
+__device__ __forceinline__ bool v2_run_extent(const In& in, uint32_t pos, uint32_t n_in, uint32_t* len,
+                                              uint32_t* end) {
+  const uint64_t hdr = in.u64(pos);
+  const uint32_t b0 = (uint32_t)hdr & 0xffu;
+  const uint32_t enc = b0 >> 6;
+  if (enc == 0) {
+    *len = (b0 & 7) + 3;
+    *end = pos + 2 + ((b0 >> 3) & 7);
+    return true;
+  }
+  const uint32_t L = ((((b0 & 1) << 8) | ((uint32_t)(hdr >> 8) & 0xffu))) + 1;
+  const uint32_t code = (b0 >> 1) & 31;
+  const uint32_t w = (enc == 3 && code == 0) ? 0u : (uint32_t)v2_width((int)code);
+  *len = L;
+  if (enc == 1) {
+    *end = pos + 2 + ((L * w + 7) >> 3);
+    return true;
+  }
+  if (enc == 2) {
+    const uint32_t b2 = (uint32_t)(hdr >> 16) & 0xffu, b3 = (uint32_t)(hdr >> 24) & 0xffu;
+    const uint32_t ew = (uint32_t)v2_closest_fixed_bits((int)((b3 >> 5) + 1) + v2_width((int)(b2 & 31)));
+    *end = pos + 4 + ((b2 >> 5) + 1) + ((L * w + 7) >> 3) + (((b3 & 31) * ew + 7) >> 3);
+    return true;
+  }
+  // DELTA: header, base varint, delta-base varint, packed deltas
+  const uint64_t x = in.u64(pos + 2);
+  const uint64_t t1 = ~x & 0x8080808080808080ull;
+  const uint64_t t2 = t1 & (t1 - 1);
+  uint32_t vb;  // bytes of both varints
+  if (t2) {
+    vb = (uint32_t)(__ffsll((long long)t2) >> 3);
+  } else {  // longer than the 8-byte window
+    uint64_t v;
+    int l1, l2;
+    if (varint_at(in, pos + 2, (int64_t)n_in - (pos + 2), &v, &l1) != ST_OK) return false;
+    if (varint_at(in, pos + 2 + l1, (int64_t)n_in - (pos + 2 + l1), &v, &l2) != ST_OK) return false;
+    vb = (uint32_t)(l1 + l2);
+  }
+  *end = pos + 2 + vb + ((w != 0 && L >= 2) ? (((L - 2) * w + 7) >> 3) : 0u);
+  return true;
+}
+
+// Staged walk (one warp) with v2_run_extent; same contract as rle_v2_walk.
+// Safe for the reason given at rle_v1_walk_staged: runs before the first
+// malformed one are skipped exactly.
+template <class In>
+__device__ __forceinline__ void rle_v2_walk_staged(const In& in, uint32_t n_in, const uint64_t* target,
+                                                   int nsplit, int64_t* split_pos, uint64_t* split_cnt,
+                                                   volatile uint32_t* published) {
+  uint32_t pos = 0;
+  uint64_t count = 0;
+  int k = 1;
+  uint64_t tk = target[1];
+  while (pos < n_in) {
+    if (count >= tk) {
+      do {
+        publish_split(k, pos, count, split_pos, split_cnt, published);
+        if (++k > nsplit) return;
+        tk = target[k];
+      } while (count >= tk);
+    }
+    uint32_t len, end;
+    if (!v2_run_extent(in, pos, n_in, &len, &end)) break;
+    count += len;
+    pos = end;
+  }
+  for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+}
+
 // Decode part of one RLE v2 chunk.  The part's stream starts at a run
 // boundary (position 0 of `in`, n_in bytes to the chunk end) whose first
 // value index is count0; it decodes every run that starts before value hi_v
