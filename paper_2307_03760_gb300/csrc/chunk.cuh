@@ -179,7 +179,7 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   // segments: about kSegValues values each, at least K, at most kMaxSeg
   uint32_t nseg = K;
   if (staged && STORE) {
-    const uint64_t want = cap_v / kSegValues;
+    const uint64_t want = cap_v / (FAMILY == 1 ? kSegValuesV1 : kSegValues);
     nseg = want < K ? K : want > (uint64_t)kMaxSeg ? (uint32_t)kMaxSeg : (uint32_t)want;
   }
   if (threadIdx.x == 0) {
@@ -217,6 +217,7 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     ok = __syncthreads_and(ok);  // CTA-uniform; also publishes warp 0's tail bytes
     StagedInput in{stage, gsrc, skew};
     V1Bitmap vb{nullptr, (uint32_t)skew, 0};
+    uint32_t nx_off = 0;  // RLE v1: stage offset of the group table (0: none)
     if (FAMILY == 1 && ok) {
       uint32_t* rank = bitmap + rle_v1_bitmap_words(stage_bytes);
       v1_build_bitmap(stage, (uint32_t)skew, (uint32_t)g.n_in, bitmap, rank,
@@ -224,12 +225,24 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
       vb.bm = bitmap;
       vb.last_word = ((uint32_t)skew + (uint32_t)g.n_in + 31) >> 5;
       __syncthreads();
+      // the group table goes to the unused tail of the stage when it fits
+      nx_off = ((uint32_t)skew + (uint32_t)g.n_in + 48 + 15) & ~15u;
+      if (nseg > 1 && nx_off + 4 * (uint32_t)g.n_in <= (uint32_t)stage_bytes) {
+        v1_build_next(stage, (uint32_t)skew, (uint32_t)g.n_in, bitmap, rank, vb.last_word,
+                      reinterpret_cast<uint32_t*>(stage + nx_off));
+        __syncthreads();
+      } else {
+        nx_off = 0;
+      }
     }
     if (!ok) {
       if (threadIdx.x == 0) *key = status_key(PartResult{ST_TIMEOUT, 0, 0});
     } else {
       if (warp == 0 && nseg > 1) {
-        if (FAMILY == 1)
+        if (FAMILY == 1 && nx_off)
+          rle_v1_walk_next(reinterpret_cast<const uint32_t*>(stage + nx_off), (uint32_t)g.n_in,
+                           target, (int)nseg - 1, split_pos, split_cnt, published);
+        else if (FAMILY == 1)
           rle_v1_walk_staged(in, bitmap, bitmap + rle_v1_bitmap_words(stage_bytes),
                              (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
                              published);

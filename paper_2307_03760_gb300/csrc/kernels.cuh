@@ -39,6 +39,7 @@ constexpr int kRleStageBytes = 32768 + 256;
 // segments of a staged RLE chunk: about kSegValues values each, at most kMaxSeg
 constexpr int kMaxSeg = 64;
 constexpr int kSegValues = 1024;
+constexpr int kSegValuesV1 = 256;  // RLE v1: a cheap walk, so finer segments
 // per-CTA extras: mbarrier, status key, published/claimed, split positions,
 // counts and targets
 constexpr int kRleCtaExtra = 24 + 3 * (kMaxSeg + 1) * 8;

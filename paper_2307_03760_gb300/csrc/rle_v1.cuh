@@ -355,6 +355,75 @@ __device__ __forceinline__ void rle_v1_walk_staged(const StagedInput& in, const 
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
+// Group table of a staged chunk, for a walk that follows one shared-memory
+// load per group: nx[p] = byte length | value count << 16 of a group whose
+// header is at position p, for every position p < n_in (a header or not;
+// the walk only reads the chain from position 0), or 0 where the group
+// cannot be skipped (it runs past the chunk or spans more than 41 bitmap
+// words).  Run: the base varint ends at the first terminator within 10 bytes
+// after the delta byte.  Literal group: its end is the (rank + cnt)-th set
+// bit, found by binary search over the rank directory.  Lenient like
+// rle_v1_walk_staged.  Built by every thread of the CTA; the caller
+// synchronises the CTA before use.
+__device__ __forceinline__ void v1_build_next(const uint8_t* stage, uint32_t skew, uint32_t n_in,
+                                              const uint32_t* bm, const uint32_t* rk,
+                                              uint32_t last_word, uint32_t* nx) {
+  for (uint32_t p = threadIdx.x; p < n_in; p += blockDim.x) {
+    const uint32_t sp = skew + p;
+    const uint32_t h = stage[sp];
+    uint32_t v = 0;
+    if (h < 0x80) {  // run: header, delta byte, base varint
+      const uint32_t q = sp + 2;
+      const uint32_t w = q >> 5;
+      const uint64_t win = ((((uint64_t)bm[w + 1]) << 32) | bm[w]) >> (q & 31);
+      const uint32_t t10 = (uint32_t)win & 0x3ffu;
+      if (t10) v = (2u + (uint32_t)__ffs(t10)) | ((h + 3u) << 16);
+    } else {  // literal group of 256 - h varints
+      const uint32_t cnt = 256u - h;
+      const uint32_t gq = sp + 1;
+      const uint32_t w0 = gq >> 5;
+      const uint32_t T = rk[w0] + __popc(bm[w0] & ((1u << (gq & 31)) - 1u)) + cnt;
+      const uint32_t t_max = w0 + 41 < last_word + 30 ? w0 + 41 : last_word + 30;
+      if (rk[t_max + 1] >= T) {
+        uint32_t lo = w0, hi = t_max;  // smallest t in [lo, hi] with rk[t + 1] >= T
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (rk[mid + 1] >= T) hi = mid;
+          else lo = mid + 1;
+        }
+        const uint32_t e = lo * 32 + select_bit(bm[lo], T - rk[lo]);
+        v = (e - sp + 1) | (cnt << 16);
+      }
+    }
+    nx[p] = v;
+  }
+}
+
+// Walk (one warp) along the group table; same contract as rle_v1_walk.
+__device__ __forceinline__ void rle_v1_walk_next(const uint32_t* nx, uint32_t n_in,
+                                                 const uint64_t* target, int nsplit,
+                                                 int64_t* split_pos, uint64_t* split_cnt,
+                                                 volatile uint32_t* published) {
+  uint32_t pos = 0;
+  uint64_t count = 0;
+  int k = 1;
+  uint64_t tk = target[1];
+  while (pos < n_in) {
+    if (count >= tk) {
+      do {
+        publish_split(k, pos, count, split_pos, split_cnt, published);
+        if (++k > nsplit) return;
+        tk = target[k];
+      } while (count >= tk);
+    }
+    const uint32_t v = nx[pos];
+    if (!v) break;
+    count += v >> 16;
+    pos += v & 0xffffu;
+  }
+  for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+}
+
 // Decode a literal group of cnt varints whose first byte is at view position
 // g straight from the terminator bitmap: lane j finds the end of varint j
 // (binary search over the warp's prefix counts, then the bit in the word),
