@@ -526,6 +526,12 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
         // consumed for a symbol it does not finish; the exact path below
         // takes every other case.
         if (GWIN && STORE) {
+          // A short non-overlapping match is loaded (lane i: byte i) when it is
+          // decoded but stored only when the next match is decoded (before
+          // that one reads its source) or the loop ends, so the load latency
+          // of the source (earlier output, in L1/L2) overlaps the decoding in
+          // between.  Literals land after the pending bytes, so order holds.
+          uint32_t pdst = 0, plen = 0, pval = 0;
           while (in.inpos + 8 <= n_in && wpos + 258 <= limit) {
             if (in.nb < 48) {
               if (!ring.ensure(in.inpos >= 8 ? in.inpos - 8 : 0, in.inpos + 8)) return ST_TIMEOUT;
@@ -534,14 +540,14 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
               in.nb |= 56;
             }
             uint32_t e = lit_tab[in.bb & LITMASK];
-            if (e & 0x8000u) {  // up to 3 literals (<= 45 bits)
+            if (e & 0x8000u) {  // up to 4 table literals (<= 10 bits each; >= 48 bits here)
               uint8_t* o = out + wpos;
               int k = 0;
               do {
                 in.consume(e & 15u);
                 if (lane == 0) o[k] = (uint8_t)(e >> 4);
                 e = lit_tab[in.bb & LITMASK];
-              } while ((e & 0x8000u) && ++k < 3);
+              } while ((e & 0x8000u) && ++k < 4);
               wpos += (uint32_t)k + ((e & 0x8000u) ? 0u : 1u);
               continue;
             }
@@ -558,8 +564,16 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
             in.consume(L + x + Ld + xd);
             uint8_t* o = out + wpos;
             const uint8_t* src = o - d;
+            if (plen) {  // store the pending match
+              if (lane < plen) out[pdst + lane] = (uint8_t)pval;
+              plen = 0;
+            }
             __syncwarp();
-            if (d >= mlen) {
+            if (d >= mlen && mlen <= 32) {
+              pval = lane < mlen ? src[lane] : 0u;
+              pdst = wpos;
+              plen = mlen;
+            } else if (d >= mlen) {
               for (uint32_t i = lane; i < mlen; i += 32) o[i] = src[i];
             } else {  // overlap: byte i repeats source byte i mod d (exact float division here)
               const float r = __frcp_ru((float)d);
@@ -573,6 +587,8 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
             }
             wpos += mlen;
           }
+          if (plen && lane < plen) out[pdst + lane] = (uint8_t)pval;
+          __syncwarp();
         }
         const bool fast = in.inpos + 8 <= n_in && wpos + 258 <= limit;
         if (in.nb < 48 && !in.refill()) return ST_TIMEOUT;
