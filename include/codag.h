@@ -60,7 +60,14 @@ typedef enum {
   CODAG_ORC_RLE_V2_I64 = 2,
   CODAG_DEFLATE_RAW = 3,
   CODAG_ORC_RLE_V1_U64 = 4,
-  CODAG_ORC_RLE_V2_U64 = 5
+  CODAG_ORC_RLE_V2_U64 = 5,
+  /* ORC byte RLE (byte columns; output bytes) and boolean RLE (byte RLE over
+   * bytes of eight booleans, most significant bit first; output one 0/1 byte
+   * per boolean, output span = number of booleans, the stream must decode to
+   * exactly ceil(span / 8) bytes).  Not evaluated in the paper; Sec. VI-A
+   * notes that other encodings can be enabled the same way. */
+  CODAG_ORC_BYTE_RLE = 6,
+  CODAG_ORC_BOOL_RLE = 7
 } codag_format;
 
 /* Call status (host side). */

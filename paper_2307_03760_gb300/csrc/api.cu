@@ -78,6 +78,8 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)rle_v2_sizes_kernel, kRleMaxSmem},
                  {(const void*)inflate_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)byte_rle_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)batch_kernel, kBatchSmem}};
     for (auto& at : attrs) {
       e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, at.bytes);
@@ -128,6 +130,7 @@ int family_of(int f) {
   if (f == CODAG_ORC_RLE_V1_I64 || f == CODAG_ORC_RLE_V1_U64) return 1;
   if (f == CODAG_ORC_RLE_V2_I64 || f == CODAG_ORC_RLE_V2_U64) return 2;
   if (f == CODAG_DEFLATE_RAW) return 3;
+  if (f == CODAG_ORC_BYTE_RLE || f == CODAG_ORC_BOOL_RLE) return 4;
   return 0;
 }
 
@@ -187,11 +190,12 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   const void* fn;
   unsigned grid, block;
   size_t smem;
-  if (fam == 3) {
+  if (fam == 3 || fam == 4) {
     grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     block = kThreads;
     smem = (size_t)kWarpsPerBlock * kDeflateWarp;
-    fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
+    if (fam == 3) fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
+    else fn = store ? (const void*)byte_rle_kernel : (const void*)byte_rle_sizes_kernel;
   } else {
     // parts per chunk: enough warps to fill the GPU, at most 16 per chunk
     int parts = g_parts_per_chunk.load();
@@ -376,10 +380,10 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
   if ((s = init_pipe(p)) != CODAG_OK) return s;
   if ((s = grow_offs(p, 2 * (n + 1))) != CODAG_OK) return s;
   w->last_n = n;
-  // a Deflate decoder is one warp (about 40 resident per SM), an RLE decoder
+  // a Deflate or byte RLE decoder is one warp (about 40 resident per SM), an RLE decoder
   // a CTA (a few per SM)
   const uint64_t min_chunks =
-      (uint64_t)w->sm_count * (family_of(format) == 3 ? 40 : 8) / kPipeDecode;
+      (uint64_t)w->sm_count * (family_of(format) >= 3 ? 40 : 8) / kPipeDecode;
   const std::vector<uint64_t> bounds = plan_slices(h_out_offsets, n, min_chunks);
   uint64_t* d_coff = p.offs;
   uint64_t* d_ooff = p.offs + (n + 1);

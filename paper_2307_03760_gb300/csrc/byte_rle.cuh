@@ -1,0 +1,65 @@
+// ORC byte RLE and boolean RLE, one warp per chunk.  CODAG Sec. VI-A: other
+// encodings are enabled through the same structure (a chunk per decoding
+// unit, the staged input stream, warp-wide writes); ORC's byte run-length
+// encoding is one.  Stream format: control byte h (int8); h >= 0: the next
+// byte repeated h + 3 times; h < 0: -h literal bytes.  Boolean RLE is byte
+// RLE over bytes of eight booleans, most significant bit first; it is
+// written out as one 0/1 byte per boolean, and its output span is the
+// number of booleans (the stream must decode to exactly ceil(span / 8)
+// bytes; the unused low bits of the last byte are dropped).
+//
+// Work split inside the warp: every lane reads the control byte (identical
+// state); a run's bytes and a literal group's bytes are written by all
+// lanes, lane i taking byte i (booleans: output byte i), as coalesced stores.
+// Status order matches the oracle: TRUNCATED before OUTPUT_OVERFLOW of the
+// same group; there is no BAD_HEADER (every control byte is valid).
+#pragma once
+
+#include "ring.cuh"
+
+namespace codag {
+
+// Decode one chunk (n_in bytes through `in`) into out; cap: the output span
+// in bytes (booleans: in booleans); STORE = false sizes the stream (booleans:
+// 8 per decoded byte).  count of the result: output bytes (or booleans).
+template <bool STORE, class In>
+__device__ PartResult byte_rle_decode(In& in, int64_t n_in, bool bools, uint8_t* __restrict__ out,
+                                      uint64_t cap) {
+  const uint32_t lane = lane_id();
+  const uint64_t cap_bytes = !STORE ? ~0ull : bools ? cap / 8 + ((cap & 7) ? 1 : 0) : cap;
+  int64_t pos = 0;
+  uint64_t count = 0;  // decoded bytes
+  while (pos < n_in) {
+    const int64_t want = n_in - pos < 130 ? n_in - pos : 130;
+    if (!in.ensure(pos, pos + want)) return part_error(ST_TIMEOUT, 0, count);
+    const int h = (int8_t)in.byte(pos);
+    const uint32_t len = h >= 0 ? (uint32_t)h + 3 : (uint32_t)(-h);
+    const int64_t src = pos + 1;  // run: the value byte; literals: the first byte
+    if (h >= 0 ? src >= n_in : n_in - src < (int64_t)len)
+      return part_error(ST_TRUNCATED, pos, bools ? 8 * count : count);
+    if (len > cap_bytes - count) return part_error(ST_OVERFLOW, pos, bools ? 8 * count : count);
+    if (STORE) {
+      const uint32_t v = in.byte(src);
+      if (!bools) {
+        uint8_t* o = out + count;
+        if (h >= 0)
+          for (uint32_t i = lane; i < len; i += 32) o[i] = (uint8_t)v;
+        else
+          for (uint32_t i = lane; i < len; i += 32) o[i] = in.byte(src + i);
+      } else {
+        const uint64_t lo = 8 * count;
+        const uint64_t hi = 8 * (count + len) < cap ? 8 * (count + len) : cap;
+        for (uint64_t j = lo + lane; j < hi; j += 32) {
+          const uint32_t b = h >= 0 ? v : in.byte(src + (int64_t)(j / 8 - count));
+          out[j] = (uint8_t)((b >> (7 - (uint32_t)(j & 7))) & 1u);
+        }
+      }
+    }
+    pos = h >= 0 ? src + 1 : src + len;
+    count += len;
+  }
+  if (STORE && count < cap_bytes) return part_error(ST_UNDERFLOW, n_in, bools ? 8 * count : count);
+  return PartResult{ST_OK, -1, bools ? 8 * count : count};
+}
+
+}  // namespace codag

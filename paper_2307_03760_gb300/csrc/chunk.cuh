@@ -41,7 +41,7 @@ __device__ __forceinline__ ChunkGeom chunk_geom(const Args& a, uint64_t c) {
     const uint64_t oe = a.out_off[c + 1];
     if (oe < g.os) { g.bad = ST_BAD_SPAN; return g; }
     g.cap = oe - g.os;
-    if (FAMILY != 3 && ((g.cap & 7) || (g.os & 7))) g.bad = ST_BAD_SPAN;
+    if (FAMILY <= 2 && ((g.cap & 7) || (g.os & 7))) g.bad = ST_BAD_SPAN;
   }
   return g;
 }
@@ -107,6 +107,8 @@ __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, 
     const int32_t st =
         inflate_decode<STORE, kLitTB, kDistTB, kWin>(ring, scratch, g.n_in, a.out + g.os, g.cap, &prod);
     r = PartResult{st, 0, prod};
+  } else if (FAMILY == 4) {
+    r = byte_rle_decode<STORE>(ring, g.n_in, format == FMT_BOOL_RLE, a.out + g.os, g.cap);
   } else {
     const uint64_t cap_v = g.cap / 8;
     int64_t base = 0;
@@ -299,9 +301,10 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   if (threadIdx.x == 0) a.status[c] = key_status(*key);
 }
 
-// Plain Deflate kernel: one warp per chunk.
-template <bool STORE>
-__device__ __forceinline__ void inflate_warp_body(const Args& a) {
+// Plain kernels with one warp per chunk: Deflate (FAMILY 3) and byte /
+// boolean RLE (FAMILY 4).
+template <int FAMILY, bool STORE>
+__device__ __forceinline__ void warp_chunk_body(const Args& a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t warp = threadIdx.x >> 5;
   const uint64_t c = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -310,7 +313,7 @@ __device__ __forceinline__ void inflate_warp_body(const Args& a) {
   DeflateRing ring;
   ring.init(region);
   const PartResult r =
-      decode_part<3, STORE>(ring, region + DeflateRing::SMEM, a, c, FMT_DEFLATE, 0, 1);
+      decode_part<FAMILY, STORE>(ring, region + DeflateRing::SMEM, a, c, a.format, 0, 1);
   if (lane_id() == 0) {
     a.status[c] = r.status;
     if (!STORE) a.sizes[c] = r.count;

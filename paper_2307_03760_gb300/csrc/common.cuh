@@ -34,6 +34,8 @@ enum Format : int {
   FMT_DEFLATE = 3,
   FMT_RLE_V1_U64 = 4,
   FMT_RLE_V2_U64 = 5,
+  FMT_BYTE_RLE = 6,
+  FMT_BOOL_RLE = 7,
 };
 
 constexpr unsigned FULL = 0xffffffffu;

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "byte_rle.cuh"
 #include "inflate.cuh"
 #include "rle_v1.cuh"
 #include "rle_v2.cuh"
@@ -98,6 +99,8 @@ __host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
 // parts, dynamic shared memory = warps * per-warp size + 16.  Deflate: one
 // warp per chunk, kWarpsPerBlock warps per CTA.  *_sizes_* decode without
 // storing and write each chunk's decoded size (RLE: one warp per CTA).
+__global__ void byte_rle_kernel(Args a);
+__global__ void byte_rle_sizes_kernel(Args a);
 __global__ void rle_v1_kernel(Args a);
 __global__ void rle_v1_sizes_kernel(Args a);
 __global__ void rle_v2_kernel(Args a);

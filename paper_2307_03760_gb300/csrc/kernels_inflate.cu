@@ -1,11 +1,16 @@
-// Plain and sizing kernels for raw Deflate: one warp per chunk.
+// Plain and sizing kernels with one warp per chunk: raw Deflate, ORC byte /
+// boolean RLE.
 #include "chunk.cuh"
 
 namespace codag {
 
-__global__ void __launch_bounds__(kThreads, 10) inflate_kernel(Args a) { inflate_warp_body<true>(a); }
+__global__ void __launch_bounds__(kThreads, 10) inflate_kernel(Args a) { warp_chunk_body<3, true>(a); }
 __global__ void __launch_bounds__(kThreads) inflate_sizes_kernel(Args a) {
-  inflate_warp_body<false>(a);
+  warp_chunk_body<3, false>(a);
+}
+__global__ void __launch_bounds__(kThreads) byte_rle_kernel(Args a) { warp_chunk_body<4, true>(a); }
+__global__ void __launch_bounds__(kThreads) byte_rle_sizes_kernel(Args a) {
+  warp_chunk_body<4, false>(a);
 }
 
 }  // namespace codag

@@ -27,6 +27,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsynth.so")
 
 RLE_V1_I64, RLE_V2_I64, DEFLATE, RLE_V1_U64, RLE_V2_U64 = 1, 2, 3, 4, 5
+BYTE_RLE, BOOL_RLE = 6, 7
 FORMAT_NAMES = {1: "rle_v1", 2: "rle_v2", 3: "deflate", 4: "rle_v1_u64", 5: "rle_v2_u64"}
 
 _lock = threading.Lock()
@@ -55,6 +56,9 @@ def lib():
                 f.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]
                 f.restype = ctypes.c_uint64
+            L.synth_byte_rle_chunk.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64]
+            L.synth_byte_rle_chunk.restype = ctypes.c_uint64
             L.synth_plaintext.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_uint64]
             L.synth_plaintext.restype = ctypes.c_int
@@ -104,6 +108,20 @@ def rle_chunk(fmt: int, seed: int, chunk: int, n_values: int, keep_values: bool 
         cap = int(used)
 
 
+def byte_rle_chunk(seed: int, chunk: int, n_bytes: int, keep_values: bool = True):
+    """Encode one generated ORC byte RLE chunk; returns (encoded, bytes or None)."""
+    L = lib()
+    vals = np.empty(max(n_bytes, 1), dtype=np.uint8) if keep_values else None
+    cap = 2 * n_bytes + 64
+    while True:
+        enc = np.empty(cap, dtype=np.uint8)
+        used = L.synth_byte_rle_chunk(seed, chunk, n_bytes, None if vals is None else vals.ctypes.data,
+                                      enc.ctypes.data, cap)
+        if used <= cap:
+            return enc[:used].copy(), (vals[:n_bytes] if vals is not None else None)
+        cap = int(used)
+
+
 def plaintext(seed: int, chunk: int, n: int, kind: int = -1) -> np.ndarray:
     out = np.empty(max(n, 1), dtype=np.uint8)
     lib().synth_plaintext(seed, chunk, kind, out.ctypes.data, n)
@@ -143,6 +161,11 @@ def build_chunks(fmts, sizes, seed: int, keep_plain: bool = False, level: int = 
         if f == DEFLATE:
             p = plaintext(seed, c, s)
             return np.frombuffer(deflate_bytes(p, level, strategy), dtype=np.uint8), p
+        if f == BYTE_RLE:
+            return byte_rle_chunk(seed, c, s, keep_plain)
+        if f == BOOL_RLE:  # s booleans: ceil(s / 8) packed bytes, expanded MSB first
+            enc, packed = byte_rle_chunk(seed, c, (s + 7) // 8, keep_plain)
+            return enc, (np.unpackbits(packed)[:s] if packed is not None else None)
         enc, vals = rle_chunk(f, seed, c, s // 8, keep_plain)
         return enc, (vals.view(np.uint8) if vals is not None else None)
 
@@ -178,6 +201,18 @@ def deflate_column(seed: int = 1, total: int = 1 * GiB, chunk: int = 64 * 1024, 
     """Raw Deflate, zlib level 6: 1 GiB in 64 KiB chunks (16384 chunks)."""
     n = total // chunk
     return build_chunks([DEFLATE] * n, [chunk] * n, seed, name="deflate", **kw)
+
+
+def byte_rle_column(seed: int = 1, total: int = 64 * MiB, chunk: int = 64 * 1024, **kw) -> Chunked:
+    """ORC byte RLE: 64 MiB of bytes in 64 KiB chunks (1024 chunks)."""
+    n = total // chunk
+    return build_chunks([BYTE_RLE] * n, [chunk] * n, seed, name="byte_rle", **kw)
+
+
+def bool_rle_column(seed: int = 1, total: int = 64 * MiB, chunk: int = 64 * 1024, **kw) -> Chunked:
+    """ORC boolean RLE: 64 Mi booleans (one output byte each) in chunks of 64 Ki."""
+    n = total // chunk
+    return build_chunks([BOOL_RLE] * n, [chunk] * n, seed, name="bool_rle", **kw)
 
 
 def batched_plan(seed: int = 1, n_chunks: int = 20000, lo: int = 4096, hi: int = MiB):

@@ -185,6 +185,45 @@ uint64_t synth_rle_v1_chunk(uint64_t seed, uint64_t chunk, int is_signed, uint64
   return w.n;
 }
 
+/* ----------------------------------------------------------- byte RLE --- */
+/* One ORC byte RLE chunk of n bytes, shaped like a low-cardinality byte or
+ * packed-boolean column: 55% runs (length uniform 3..130, value from a
+ * 16-symbol alphabet), 45% literal groups (1..128 bytes, 3/4 from the
+ * alphabet, 1/4 uniform).  Same calling convention as synth_rle_v1_chunk,
+ * with the decoded bytes in `values`. */
+uint64_t synth_byte_rle_chunk(uint64_t seed, uint64_t chunk, uint64_t n, uint8_t *values,
+                              uint8_t *enc, uint64_t cap) {
+  rng_t r = rng_make(seed, 5, chunk);
+  wbuf w = {enc, 0, cap, 0};
+  uint8_t alpha[16];
+  for (int i = 0; i < 16; i++) alpha[i] = (uint8_t)rng_next(&r);
+  uint64_t pos = 0;
+  while (pos < n) {
+    uint64_t rem = n - pos;
+    if (rem >= 3 && rng_below(&r, 100) < 55) {
+      uint64_t len = (uint64_t)rng_range(&r, 3, 130);
+      if (len > rem) len = rem;
+      uint8_t v = alpha[rng_below(&r, 16)];
+      put_byte(&w, (uint8_t)(len - 3));
+      put_byte(&w, v);
+      for (uint64_t i = 0; i < len; i++)
+        if (values) values[pos + i] = v;
+      pos += len;
+    } else {
+      uint64_t cnt = (uint64_t)rng_range(&r, 1, 128);
+      if (cnt > rem) cnt = rem;
+      put_byte(&w, (uint8_t)(256 - cnt));
+      for (uint64_t i = 0; i < cnt; i++) {
+        uint8_t v = rng_below(&r, 4) ? alpha[rng_below(&r, 16)] : (uint8_t)rng_next(&r);
+        put_byte(&w, v);
+        if (values) values[pos + i] = v;
+      }
+      pos += cnt;
+    }
+  }
+  return w.n;
+}
+
 /* ------------------------------------------------------------- RLE v2 --- */
 static void v2_header2(wbuf *w, int enc, int wcode, uint64_t len) {
   put_byte(w, (uint8_t)((enc << 6) | (wcode << 1) | (int)((len - 1) >> 8)));

@@ -36,6 +36,45 @@ def expected_rle(case) -> bytes:
     return b"".join(((v & MASK64).to_bytes(8, "little")) for v in vals)
 
 
+def expected_byte_rle(case) -> bytes:
+    """Expected output of a byte / boolean RLE golden case."""
+    if "bits" in case:
+        return bytes(int(b) for b in case["bits"])
+    if "fill_bytes" in case:
+        return b"".join(bytes([v]) * k for v, k in case["fill_bytes"])
+    return bytes.fromhex(case.get("out_hex", "").replace(" ", ""))
+
+
+def byte_rle_encode(data: bytes) -> bytes:
+    """Independent greedy ORC byte RLE encoder (runs of >= 3 equal bytes,
+    everything else in literal groups of up to 128), for round trips."""
+    out = bytearray()
+    lit = bytearray()
+    i, n = 0, len(data)
+
+    def flush():
+        while lit:
+            k = min(len(lit), 128)
+            out.append(256 - k)
+            out.extend(lit[:k])
+            del lit[:k]
+
+    while i < n:
+        j = i
+        while j < n and j - i < 130 and data[j] == data[i]:
+            j += 1
+        if j - i >= 3:
+            flush()
+            out.append(j - i - 3)
+            out.append(data[i])
+            i = j
+        else:
+            lit.append(data[i])
+            i += 1
+    flush()
+    return bytes(out)
+
+
 def expected_deflate(case) -> bytes:
     if "text" in case:
         return case["text"].encode()

@@ -54,12 +54,14 @@ def _check(w, got, st, comp=None):
 
 @pytest.mark.parametrize("name,total,chunk", [("rle_v1", 8 * synth.MiB, 65536),
                                               ("rle_v2", 72 * synth.MiB, 8192),
-                                              ("deflate", 40 * synth.MiB, 4096)])
+                                              ("deflate", 40 * synth.MiB, 4096),
+                                              ("byte_rle", 40 * synth.MiB, 10240)])
 def test_host_columns(name, total, chunk):
     """Small chunks, so that the columns are cut into several slices (one for
     the 8 MiB RLE v1 column)."""
     w = {"rle_v1": synth.rle_v1_column, "rle_v2": synth.rle_v2_column,
-         "deflate": synth.deflate_column}[name](seed=5, total=total, chunk=chunk)
+         "deflate": synth.deflate_column, "byte_rle": synth.byte_rle_column}[name](
+        seed=5, total=total, chunk=chunk)
     got, st = _run_host(w)
     assert (st == 0).all()
     _check(w, got, st)
