@@ -213,6 +213,8 @@ def workload(name: str, seed: int):
         return synth.byte_rle_column(seed, total=int(64 * synth.MiB * SCALE) // 65536 * 65536 or 65536)
     if name == "bool_rle":
         return synth.bool_rle_column(seed, total=int(64 * synth.MiB * SCALE) // 65536 * 65536 or 65536)
+    if name == "orc_zlib":
+        return synth.orc_zlib_column(seed, total=int(synth.GiB * SCALE) // 262144 * 262144 or 262144)
     raise ValueError(name)
 
 
@@ -223,8 +225,9 @@ WORKLOAD_DESC = {
     "batched": "mixed_batch_20000_chunks_4KiB_1MiB",
     "byte_rle": "orc_byte_rle_64MiB_64KiB_chunks",
     "bool_rle": "orc_bool_rle_64Mi_booleans_64Ki_per_chunk",
+    "orc_zlib": "orc_zlib_streams_1GiB_256KiB_streams_64KiB_blocks",
 }
-FMT_OF = {"rle_v1": 1, "rle_v2": 2, "deflate": 3, "byte_rle": 6, "bool_rle": 7}
+FMT_OF = {"rle_v1": 1, "rle_v2": 2, "deflate": 3, "byte_rle": 6, "bool_rle": 7, "orc_zlib": 8}
 
 
 def run_reference(args, world, rank):
@@ -375,7 +378,7 @@ def main():
     achieved = d.alg_bytes() / (kernel_ms / 1e3) / 1e9
     kernel = {"rle_v1": "rle_v1_kernel", "rle_v2": "rle_v2_kernel", "deflate": "inflate_kernel",
               "batched": "batch_kernel", "byte_rle": "byte_rle_kernel",
-              "bool_rle": "byte_rle_kernel"}[name]
+              "bool_rle": "byte_rle_kernel", "orc_zlib": "orc_zlib_kernel"}[name]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic_from_profile(kernel, w.n), "kernel": kernel,
@@ -485,7 +488,7 @@ def serving(torch, seconds: float):
 
 def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
     res = {headline: {"GBps": round(hvalue, 2), "hbm_frac": round(hach / peak, 4)}}
-    for name in ("rle_v1", "deflate", "byte_rle", "bool_rle"):
+    for name in ("rle_v1", "deflate", "byte_rle", "bool_rle", "orc_zlib"):
         if name == headline:
             continue
         w = workload(name, 1)
@@ -497,7 +500,7 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
         fn()
         torch.cuda.synchronize()
         st = codag.codag_last_chunk_status(w.n)
-        ms = time_steps(torch, stream, fn, 10 if name == "deflate" else 100, 3)
+        ms = time_steps(torch, stream, fn, 10 if name in ("deflate", "orc_zlib") else 100, 3)
         t = statistics.median(ms)
         res[name] = {"GBps": round(w.out_bytes / (t / 1e3) / 1e9, 2),
                      "hbm_frac": round(d.alg_bytes() / (t / 1e3) / 1e9 / peak, 4),

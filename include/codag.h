@@ -67,7 +67,13 @@ typedef enum {
    * exactly ceil(span / 8) bytes).  Not evaluated in the paper; Sec. VI-A
    * notes that other encodings can be enabled the same way. */
   CODAG_ORC_BYTE_RLE = 6,
-  CODAG_ORC_BOOL_RLE = 7
+  CODAG_ORC_BOOL_RLE = 7,
+  /* An ORC compressed stream with zlib compression: compression chunks of a
+   * 3-byte little-endian header v (v >> 1 body bytes follow; bit 0 set: the
+   * body is stored as is, clear: it is a raw Deflate stream of its own) and
+   * the body; the output is the bodies' decoded bytes in order (Sec. I and
+   * II-B: data decoded as existing systems store it). */
+  CODAG_ORC_ZLIB = 8
 } codag_format;
 
 /* Call status (host side). */

@@ -23,14 +23,14 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = ["rle_v1.c", "rle_v2.c", "inflate.c", "byte_rle.c", "batch.c"]
+SOURCES = ["rle_v1.c", "rle_v2.c", "inflate.c", "byte_rle.c", "orc_frames.c", "batch.c"]
 
 # Status codes (numeric values shared with the library's per-chunk status).
 OK, TRUNCATED, OUTPUT_OVERFLOW, OUTPUT_UNDERFLOW = 0, 1, 2, 3
 BAD_HEADER, BAD_HUFFMAN, BAD_DISTANCE, BAD_STORED_LEN, BAD_SPAN = 4, 5, 6, 7, 8
 
 FMT_RLE_V1_I64, FMT_RLE_V2_I64, FMT_DEFLATE, FMT_RLE_V1_U64, FMT_RLE_V2_U64 = 1, 2, 3, 4, 5
-FMT_BYTE_RLE, FMT_BOOL_RLE = 6, 7
+FMT_BYTE_RLE, FMT_BOOL_RLE, FMT_ORC_ZLIB = 6, 7, 8
 
 _lock = threading.Lock()
 _lib = None

@@ -19,6 +19,7 @@ int oracle_decode_chunk(int format, const uint8_t *in, size_t n_in,
     case ORC_FMT_DEFLATE: return oracle_inflate(in, n_in, out, cap, n_out);
     case ORC_FMT_BYTE_RLE: return oracle_byte_rle(in, n_in, out, cap, n_out);
     case ORC_FMT_BOOL_RLE: return oracle_bool_rle(in, n_in, out, cap, n_out);
+    case ORC_FMT_ORC_ZLIB: return oracle_orc_zlib(in, n_in, out, cap, n_out);
     default: *n_out = 0; return ORC_BAD_HEADER;
   }
 }

@@ -50,7 +50,8 @@ enum {
   ORC_FMT_RLE_V1_U64 = 4,
   ORC_FMT_RLE_V2_U64 = 5,
   ORC_FMT_BYTE_RLE = 6,  /* ORC byte RLE: bytes out                        */
-  ORC_FMT_BOOL_RLE = 7   /* ORC boolean RLE: one 0/1 byte per boolean out  */
+  ORC_FMT_BOOL_RLE = 7,  /* ORC boolean RLE: one 0/1 byte per boolean out  */
+  ORC_FMT_ORC_ZLIB = 8   /* ORC compressed stream: 3-byte framed Deflate   */
 };
 
 /*
@@ -70,6 +71,7 @@ int oracle_inflate(const uint8_t *in, size_t n_in,
 int oracle_byte_rle(const uint8_t *in, size_t n_in, uint8_t *out, size_t cap, size_t *n_out);
 /* cap = number of booleans; sizing (out = NULL) gives 8 per decoded byte */
 int oracle_bool_rle(const uint8_t *in, size_t n_in, uint8_t *out, size_t cap, size_t *n_out);
+int oracle_orc_zlib(const uint8_t *in, size_t n_in, uint8_t *out, size_t cap, size_t *n_out);
 
 /* Dispatch on a format identifier (unknown format -> ORC_BAD_HEADER). */
 int oracle_decode_chunk(int format, const uint8_t *in, size_t n_in,

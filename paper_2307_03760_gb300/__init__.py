@@ -22,8 +22,9 @@ CODAG_ORC_RLE_V1_U64 = 4
 CODAG_ORC_RLE_V2_U64 = 5
 CODAG_ORC_BYTE_RLE = 6
 CODAG_ORC_BOOL_RLE = 7
+CODAG_ORC_ZLIB = 8
 FORMATS = {"rle_v1": 1, "rle_v2": 2, "deflate": 3, "rle_v1_u64": 4, "rle_v2_u64": 5,
-           "byte_rle": 6, "bool_rle": 7}
+           "byte_rle": 6, "bool_rle": 7, "orc_zlib": 8}
 
 CODAG_OK, CODAG_EINVAL, CODAG_ECUDA, CODAG_ENOMEM, CODAG_ECORRUPT, CODAG_ETIMEOUT = range(6)
 CHUNK_STATUS = ["OK", "TRUNCATED", "OUTPUT_OVERFLOW", "OUTPUT_UNDERFLOW", "BAD_HEADER",

@@ -78,6 +78,8 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)rle_v2_sizes_kernel, kRleMaxSmem},
                  {(const void*)inflate_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)orc_zlib_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)orc_zlib_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)byte_rle_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)batch_kernel, kBatchSmem}};
@@ -131,6 +133,7 @@ int family_of(int f) {
   if (f == CODAG_ORC_RLE_V2_I64 || f == CODAG_ORC_RLE_V2_U64) return 2;
   if (f == CODAG_DEFLATE_RAW) return 3;
   if (f == CODAG_ORC_BYTE_RLE || f == CODAG_ORC_BOOL_RLE) return 4;
+  if (f == CODAG_ORC_ZLIB) return 5;
   return 0;
 }
 
@@ -190,12 +193,13 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   const void* fn;
   unsigned grid, block;
   size_t smem;
-  if (fam == 3 || fam == 4) {
+  if (fam >= 3) {
     grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     block = kThreads;
     smem = (size_t)kWarpsPerBlock * kDeflateWarp;
     if (fam == 3) fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
-    else fn = store ? (const void*)byte_rle_kernel : (const void*)byte_rle_sizes_kernel;
+    else if (fam == 4) fn = store ? (const void*)byte_rle_kernel : (const void*)byte_rle_sizes_kernel;
+    else fn = store ? (const void*)orc_zlib_kernel : (const void*)orc_zlib_sizes_kernel;
   } else {
     // parts per chunk: enough warps to fill the GPU, at most 16 per chunk
     int parts = g_parts_per_chunk.load();

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "orc_frames.cuh"  // after kernels.cuh: uses the Deflate table sizes
 
 namespace codag {
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ void walk_to(In& in, uint8_t* scratch, int64_t n_in, 
 
 // Part k of K of chunk c through a per-warp staging ring (batch kernel): the
 // warp walks to its start, then decodes its runs from there.
-template <int FAMILY, bool STORE, class Ring>
+template <int FAMILY, bool STORE, class Ring, int WIN = kWin>
 __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, const Args& a,
                                                   uint64_t c, int format, uint32_t k, uint32_t K) {
   const ChunkGeom g = chunk_geom<FAMILY, STORE>(a, c);
@@ -105,10 +106,12 @@ __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, 
   if (FAMILY == 3) {
     uint64_t prod = 0;
     const int32_t st =
-        inflate_decode<STORE, kLitTB, kDistTB, kWin>(ring, scratch, g.n_in, a.out + g.os, g.cap, &prod);
+        inflate_decode<STORE, kLitTB, kDistTB, WIN>(ring, scratch, g.n_in, a.out + g.os, g.cap, &prod);
     r = PartResult{st, 0, prod};
   } else if (FAMILY == 4) {
     r = byte_rle_decode<STORE>(ring, g.n_in, format == FMT_BOOL_RLE, a.out + g.os, g.cap);
+  } else if (FAMILY == 5) {
+    r = orc_zlib_decode<STORE>(ring, scratch, g.n_in, a.out + g.os, g.cap);
   } else {
     const uint64_t cap_v = g.cap / 8;
     int64_t base = 0;
@@ -301,8 +304,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   if (threadIdx.x == 0) a.status[c] = key_status(*key);
 }
 
-// Plain kernels with one warp per chunk: Deflate (FAMILY 3) and byte /
-// boolean RLE (FAMILY 4).
+// Plain kernels with one warp per chunk: Deflate (FAMILY 3), byte /
+// boolean RLE (FAMILY 4) and ORC zlib streams (FAMILY 5).
 template <int FAMILY, bool STORE>
 __device__ __forceinline__ void warp_chunk_body(const Args& a) {
   extern __shared__ __align__(128) uint8_t smem[];

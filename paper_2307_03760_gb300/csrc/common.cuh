@@ -36,6 +36,7 @@ enum Format : int {
   FMT_RLE_V2_U64 = 5,
   FMT_BYTE_RLE = 6,
   FMT_BOOL_RLE = 7,
+  FMT_ORC_ZLIB = 8,
 };
 
 constexpr unsigned FULL = 0xffffffffu;

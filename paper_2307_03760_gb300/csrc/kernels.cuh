@@ -51,8 +51,13 @@ __host__ __device__ constexpr int rle_v1_bitmap_words(int stage_bytes) { return 
 __host__ __device__ constexpr int rle_v1_bitmap_bytes(int stage_bytes) { return (2 * rle_v1_bitmap_words(stage_bytes) + 32) * 4; }
 constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra +
                             rle_v1_bitmap_bytes(16 * RleRing::SMEM);
+// Deflate in the batch kernel may keep recent output in a shared window
+// (kBatchWin bytes, 0 = none): the batch ends on its largest Deflate chunks,
+// decoded one warp each, where match latency rather than occupancy decides.
+constexpr int kBatchWin = 0;
+using BatchDeflateSmem = InflateSmem<kLitTB, kDistTB, kBatchWin>;
 constexpr int kBatchWarp =
-    round128(RleRing::SMEM + cmax(DeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
+    round128(RleRing::SMEM + cmax(BatchDeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
 
 struct Args {
   const uint8_t* comp;
@@ -99,6 +104,8 @@ __host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
 // parts, dynamic shared memory = warps * per-warp size + 16.  Deflate: one
 // warp per chunk, kWarpsPerBlock warps per CTA.  *_sizes_* decode without
 // storing and write each chunk's decoded size (RLE: one warp per CTA).
+__global__ void orc_zlib_kernel(Args a);
+__global__ void orc_zlib_sizes_kernel(Args a);
 __global__ void byte_rle_kernel(Args a);
 __global__ void byte_rle_sizes_kernel(Args a);
 __global__ void rle_v1_kernel(Args a);

@@ -89,9 +89,11 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(Args a) {
     else if (f == FMT_RLE_V2_I64 || f == FMT_RLE_V2_U64)
       r = decode_part<2, true>(ring, scratch, a, c, f, part, parts);
     else if (f == FMT_DEFLATE)
-      r = decode_part<3, true>(ring, scratch, a, c, f, 0, 1);
+      r = decode_part<3, true, RleRing, kBatchWin>(ring, scratch, a, c, f, 0, 1);
     else if (f == FMT_BYTE_RLE || f == FMT_BOOL_RLE)
       r = decode_part<4, true>(ring, scratch, a, c, f, 0, 1);
+    else if (f == FMT_ORC_ZLIB)
+      r = decode_part<5, true>(ring, scratch, a, c, f, 0, 1);
     else
       r = PartResult{ST_BAD_HEADER, 0, 0};
     if (lane_id() == 0) {

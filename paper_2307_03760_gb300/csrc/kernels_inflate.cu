@@ -1,5 +1,5 @@
-// Plain and sizing kernels with one warp per chunk: raw Deflate, ORC byte /
-// boolean RLE.
+// Plain and sizing kernels with one warp per chunk: raw Deflate, ORC zlib
+// streams, ORC byte / boolean RLE.
 #include "chunk.cuh"
 
 namespace codag {
@@ -7,6 +7,10 @@ namespace codag {
 __global__ void __launch_bounds__(kThreads, 10) inflate_kernel(Args a) { warp_chunk_body<3, true>(a); }
 __global__ void __launch_bounds__(kThreads) inflate_sizes_kernel(Args a) {
   warp_chunk_body<3, false>(a);
+}
+__global__ void __launch_bounds__(kThreads, 10) orc_zlib_kernel(Args a) { warp_chunk_body<5, true>(a); }
+__global__ void __launch_bounds__(kThreads) orc_zlib_sizes_kernel(Args a) {
+  warp_chunk_body<5, false>(a);
 }
 __global__ void __launch_bounds__(kThreads) byte_rle_kernel(Args a) { warp_chunk_body<4, true>(a); }
 __global__ void __launch_bounds__(kThreads) byte_rle_sizes_kernel(Args a) {

@@ -201,6 +201,12 @@ struct OffsetIn {
   __device__ __forceinline__ uint64_t u64(int64_t p) const { return in->u64(p + base); }
 };
 
+// The same view over a staging ring, for decoders that need the ring's span.
+template <class Ring>
+struct OffsetRing : OffsetIn<Ring> {
+  static constexpr int MAX_SPAN = Ring::MAX_SPAN;
+};
+
 // Bytes a staged chunk of n_in bytes needs: 16-byte alignment skew in front,
 // and reads of up to 16 bytes past the last position (stale but in bounds).
 __host__ __device__ __forceinline__ int64_t staged_bytes(int64_t n_in) { return n_in + 15 + 32; }

@@ -27,7 +27,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "libsynth.so")
 
 RLE_V1_I64, RLE_V2_I64, DEFLATE, RLE_V1_U64, RLE_V2_U64 = 1, 2, 3, 4, 5
-BYTE_RLE, BOOL_RLE = 6, 7
+BYTE_RLE, BOOL_RLE, ORC_ZLIB = 6, 7, 8
 FORMAT_NAMES = {1: "rle_v1", 2: "rle_v2", 3: "deflate", 4: "rle_v1_u64", 5: "rle_v2_u64"}
 
 _lock = threading.Lock()
@@ -122,6 +122,26 @@ def byte_rle_chunk(seed: int, chunk: int, n_bytes: int, keep_values: bool = True
         cap = int(used)
 
 
+def orc_frame(body: bytes, original: bool) -> bytes:
+    """One ORC compression chunk: 3-byte little-endian header (length << 1 |
+    original) and the body."""
+    v = (len(body) << 1) | (1 if original else 0)
+    return bytes((v & 0xFF, (v >> 8) & 0xFF, (v >> 16) & 0xFF)) + body
+
+
+def orc_zlib_stream(data, block: int = 64 * 1024, level: int = 6) -> bytes:
+    """An ORC compressed stream as an ORC writer makes it: the data cut into
+    blocks, each compressed as raw Deflate, or stored as is when that is not
+    smaller."""
+    data = bytes(data)
+    out = []
+    for i in range(0, len(data), block):
+        piece = data[i:i + block]
+        comp = deflate_bytes(piece, level)
+        out.append(orc_frame(comp, False) if len(comp) < len(piece) else orc_frame(piece, True))
+    return b"".join(out)
+
+
 def plaintext(seed: int, chunk: int, n: int, kind: int = -1) -> np.ndarray:
     out = np.empty(max(n, 1), dtype=np.uint8)
     lib().synth_plaintext(seed, chunk, kind, out.ctypes.data, n)
@@ -163,6 +183,9 @@ def build_chunks(fmts, sizes, seed: int, keep_plain: bool = False, level: int = 
             return np.frombuffer(deflate_bytes(p, level, strategy), dtype=np.uint8), p
         if f == BYTE_RLE:
             return byte_rle_chunk(seed, c, s, keep_plain)
+        if f == ORC_ZLIB:  # ORC stream of 64 KiB compression blocks
+            p = plaintext(seed, c, s)
+            return np.frombuffer(orc_zlib_stream(p, 64 * 1024, level), dtype=np.uint8), p
         if f == BOOL_RLE:  # s booleans: ceil(s / 8) packed bytes, expanded MSB first
             enc, packed = byte_rle_chunk(seed, c, (s + 7) // 8, keep_plain)
             return enc, (np.unpackbits(packed)[:s] if packed is not None else None)
@@ -213,6 +236,13 @@ def bool_rle_column(seed: int = 1, total: int = 64 * MiB, chunk: int = 64 * 1024
     """ORC boolean RLE: 64 Mi booleans (one output byte each) in chunks of 64 Ki."""
     n = total // chunk
     return build_chunks([BOOL_RLE] * n, [chunk] * n, seed, name="bool_rle", **kw)
+
+
+def orc_zlib_column(seed: int = 1, total: int = 1 * GiB, chunk: int = 256 * 1024, **kw) -> Chunked:
+    """ORC zlib streams: 1 GiB as 4096 streams of 256 KiB, each four 64 KiB
+    compression blocks (raw Deflate level 6, stored when not smaller)."""
+    n = total // chunk
+    return build_chunks([ORC_ZLIB] * n, [chunk] * n, seed, name="orc_zlib", **kw)
 
 
 def batched_plan(seed: int = 1, n_chunks: int = 20000, lo: int = 4096, hi: int = MiB):
