@@ -289,6 +289,20 @@ int codag_get_batch_ctas_per_sm(void);
 codag_status codag_set_parts_per_chunk(int parts);
 int codag_get_parts_per_chunk(void);
 
+/*
+ * Input staging of the one-warp-per-chunk decode kernels (CODAG Sec. V-E and
+ * its register input buffer): mode 0 stages compressed bytes in a per-warp
+ * shared-memory ring filled by TMA bulk copies (default); mode 1 keeps a
+ * 512-byte window in the warp's registers, refilled by coalesced loads, and
+ * reads it with __shfl_sync (no shared memory for the input).  format: a
+ * Deflate or byte / boolean RLE format (the setting is per decoder family;
+ * RLE v1/v2 always stage in shared memory).  Process-wide; an autotuner
+ * choice.  Returns CODAG_EINVAL for another format or mode; the getter
+ * returns -1 for another format.
+ */
+codag_status codag_set_input_staging(int format, int mode);
+int codag_get_input_staging(int format);
+
 /* Number of kernel launches the library enqueued since load (all calls). */
 uint64_t codag_kernel_launches(void);
 

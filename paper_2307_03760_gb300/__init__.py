@@ -72,6 +72,10 @@ def lib() -> ctypes.CDLL:
         L.codag_set_batch_ctas_per_sm.argtypes = [i32]
         L.codag_set_parts_per_chunk.argtypes = [i32]
         L.codag_get_parts_per_chunk.restype = i32
+        L.codag_set_input_staging.argtypes = [i32, i32]
+        L.codag_set_input_staging.restype = i32
+        L.codag_get_input_staging.argtypes = [i32]
+        L.codag_get_input_staging.restype = i32
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
                      "codag_decompress_host",
                      "codag_last_chunk_status", "codag_batch_graph_create",
@@ -232,6 +236,15 @@ def codag_get_batch_ctas_per_sm() -> int:
 
 def codag_set_parts_per_chunk(k: int):
     _check(lib().codag_set_parts_per_chunk(int(k)), "codag_set_parts_per_chunk")
+
+
+def codag_set_input_staging(fmt, mode: int):
+    """0: shared-memory TMA ring, 1: register ring (Deflate, byte / boolean RLE)."""
+    _check(lib().codag_set_input_staging(_fmt(fmt), mode), "codag_set_input_staging")
+
+
+def codag_get_input_staging(fmt) -> int:
+    return lib().codag_get_input_staging(_fmt(fmt))
 
 
 def codag_get_parts_per_chunk() -> int:

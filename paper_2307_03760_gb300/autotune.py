@@ -1,8 +1,10 @@
 """Autotuner for the launch shapes the library leaves open.
 
-Two knobs: parts per RLE chunk for the plain RLE calls (warps cooperating on
-one chunk; ``codag_set_parts_per_chunk``) and resident CTAs per SM of the
-persistent batch kernel (decoders per SM; ``codag_set_batch_ctas_per_sm``).
+Three knobs: parts per RLE chunk for the plain RLE calls (warps cooperating
+on one chunk; ``codag_set_parts_per_chunk``), resident CTAs per SM of the
+persistent batch kernel (decoders per SM; ``codag_set_batch_ctas_per_sm``),
+and the input staging of the one-warp-per-chunk decoders (shared-memory TMA
+ring or register ring; ``codag_set_input_staging``) for Deflate and byte RLE.
 ``sweep`` times every candidate on a workload with CUDA events and keeps the
 fastest; ``tune`` runs the sweeps and writes a table, ``apply`` loads a
 table into the library.  The selection is separated from the timing so it
@@ -80,6 +82,18 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1) -> dict:
         table["rle_parts"][name] = {"chunks": w.n, "best": best, "ms": round(ms, 4)}
         table["sweeps"][f"{name}_parts"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}
     codag.codag_set_parts_per_chunk(0)
+    # input staging of the one-warp-per-chunk decoders (0: shared ring, 1: registers)
+    table["input_staging"] = {}
+    for name, w in (("deflate", synth.deflate_column(seed, total=256 * synth.MiB)),
+                    ("byte_rle", synth.byte_rle_column(seed))):
+        comp, coff, ooff, _, out, _ = upload(w)
+        fmt = int(w.formats[0])
+        run = lambda: codag.codag_decompress(fmt, comp, coff, w.n, out, ooff)  # noqa: E731
+        t = sweep(run, [0, 1], lambda m: codag.codag_set_input_staging(fmt, m), reps=5, timer=timer)
+        best, ms = choose(t)
+        table["input_staging"][name] = {"format": fmt, "best": best, "ms": round(ms, 4)}
+        table["sweeps"][f"{name}_input_staging"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}
+        codag.codag_set_input_staging(fmt, 0)
     # the full mixed batch: a sample of it would be dominated by its largest
     # chunk and favour too few CTAs
     w = synth.batched(seed)
@@ -114,6 +128,11 @@ def apply(path: str = DEFAULT_TABLE, n_chunks: int | None = None, family: str = 
     if p and (n_chunks is None or p.get("chunks") == n_chunks):
         codag.codag_set_parts_per_chunk(int(p["best"]))
         done["parts_per_chunk"] = int(p["best"])
+    for name, e in table.get("input_staging", {}).items():
+        codag.codag_set_input_staging(int(e["format"]), int(e["best"]))
+        if int(e["format"]) == 6:  # boolean RLE runs the same decoder
+            codag.codag_set_input_staging(7, int(e["best"]))
+        done[f"input_staging_{name}"] = int(e["best"])
     return done
 
 

@@ -18,6 +18,7 @@ thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_batch_ctas_per_sm{0};
 std::atomic<int> g_parts_per_chunk{0};
+std::atomic<int> g_reg_ring[8];  // per decoder family: 1 = register staging ring
 
 codag_status fail(codag_status s, const std::string& msg) {
   g_last_error = msg;
@@ -80,8 +81,9 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
-                 {(const void*)byte_rle_kernel, kWarpsPerBlock * kDeflateWarp},
-                 {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
+                 {(const void*)byte_rle_kernel, kWarpsPerBlock * warp_chunk_smem(4, DeflateRing::SMEM)},
+                 {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, DeflateRing::SMEM)},
+                 {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
                  {(const void*)batch_kernel, kBatchSmem}};
     for (auto& at : attrs) {
       e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, at.bytes);
@@ -196,10 +198,16 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   if (fam >= 3) {
     grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     block = kThreads;
-    smem = (size_t)kWarpsPerBlock * kDeflateWarp;
-    if (fam == 3) fn = store ? (const void*)inflate_kernel : (const void*)inflate_sizes_kernel;
-    else if (fam == 4) fn = store ? (const void*)byte_rle_kernel : (const void*)byte_rle_sizes_kernel;
-    else fn = store ? (const void*)orc_zlib_kernel : (const void*)orc_zlib_sizes_kernel;
+    // decode kernels of Deflate and byte / boolean RLE may stage their input
+    // in registers instead of a shared-memory ring (codag_set_input_staging)
+    const bool reg = store && (fam == 3 || fam == 4) && g_reg_ring[fam].load() == 1;
+    smem = (size_t)kWarpsPerBlock * warp_chunk_smem(fam == 5 ? 3 : fam, reg ? 0 : DeflateRing::SMEM);
+    if (fam == 3)
+      fn = !store ? (const void*)inflate_sizes_kernel : reg ? (const void*)inflate_reg_kernel : (const void*)inflate_kernel;
+    else if (fam == 4)
+      fn = !store ? (const void*)byte_rle_sizes_kernel : reg ? (const void*)byte_rle_reg_kernel : (const void*)byte_rle_kernel;
+    else
+      fn = store ? (const void*)orc_zlib_kernel : (const void*)orc_zlib_sizes_kernel;
   } else {
     // parts per chunk: enough warps to fill the GPU, at most 16 per chunk
     int parts = g_parts_per_chunk.load();
@@ -601,6 +609,19 @@ codag_status codag_set_parts_per_chunk(int parts) {
 }
 
 int codag_get_parts_per_chunk(void) { return g_parts_per_chunk.load(); }
+
+codag_status codag_set_input_staging(int format, int mode) {
+  const int fam = family_of(format);
+  if (fam != 3 && fam != 4) return fail(CODAG_EINVAL, "input staging applies to Deflate and byte / boolean RLE");
+  if (mode != 0 && mode != 1) return fail(CODAG_EINVAL, "input staging mode: 0 (shared ring) or 1 (registers)");
+  g_reg_ring[fam].store(mode);
+  return CODAG_OK;
+}
+
+int codag_get_input_staging(int format) {
+  const int fam = family_of(format);
+  return (fam == 3 || fam == 4) ? g_reg_ring[fam].load() : -1;
+}
 
 uint64_t codag_kernel_launches(void) { return g_launches.load(); }
 

@@ -42,16 +42,23 @@ __device__ PartResult byte_rle_decode(In& in, int64_t n_in, bool bools, uint8_t*
       const uint32_t v = in.byte(src);
       if (!bools) {
         uint8_t* o = out + count;
-        if (h >= 0)
+        if (h >= 0) {
           for (uint32_t i = lane; i < len; i += 32) o[i] = (uint8_t)v;
-        else
-          for (uint32_t i = lane; i < len; i += 32) o[i] = in.byte(src + i);
+        } else {  // every lane reads in every step (a register ring reads by shuffles)
+          for (uint32_t ib = 0; ib < len; ib += 32) {
+            const uint32_t i = ib + lane;
+            const uint8_t b = in.byte(src + (i < len ? i : len - 1));
+            if (i < len) o[i] = b;
+          }
+        }
       } else {
         const uint64_t lo = 8 * count;
         const uint64_t hi = 8 * (count + len) < cap ? 8 * (count + len) : cap;
-        for (uint64_t j = lo + lane; j < hi; j += 32) {
-          const uint32_t b = h >= 0 ? v : in.byte(src + (int64_t)(j / 8 - count));
-          out[j] = (uint8_t)((b >> (7 - (uint32_t)(j & 7))) & 1u);
+        for (uint64_t jb = lo; jb < hi; jb += 32) {
+          const uint64_t j = jb + lane;
+          const uint64_t jj = j < hi ? j : hi - 1;
+          const uint32_t b = h >= 0 ? v : in.byte(src + (int64_t)(jj / 8 - count));
+          if (j < hi) out[j] = (uint8_t)((b >> (7 - (uint32_t)(j & 7))) & 1u);
         }
       }
     }

@@ -306,17 +306,20 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
 
 // Plain kernels with one warp per chunk: Deflate (FAMILY 3), byte /
 // boolean RLE (FAMILY 4) and ORC zlib streams (FAMILY 5).
-template <int FAMILY, bool STORE>
+// Ring: the shared-memory TMA ring (DeflateRing) or the register ring
+// (RegRing, no shared memory for the input); per-warp shared memory holds
+// the ring and the decoder scratch (Deflate tables; none for byte RLE).
+template <int FAMILY, bool STORE, class Ring = DeflateRing>
 __device__ __forceinline__ void warp_chunk_body(const Args& a) {
   extern __shared__ __align__(128) uint8_t smem[];
+  constexpr int kWarpSmem = warp_chunk_smem(FAMILY, Ring::SMEM);
   const uint32_t warp = threadIdx.x >> 5;
   const uint64_t c = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (c >= a.n) return;
-  uint8_t* region = smem + warp * kDeflateWarp;
-  DeflateRing ring;
+  uint8_t* region = smem + warp * kWarpSmem;
+  Ring ring;
   ring.init(region);
-  const PartResult r =
-      decode_part<FAMILY, STORE>(ring, region + DeflateRing::SMEM, a, c, a.format, 0, 1);
+  const PartResult r = decode_part<FAMILY, STORE>(ring, region + Ring::SMEM, a, c, a.format, 0, 1);
   if (lane_id() == 0) {
     a.status[c] = r.status;
     if (!STORE) a.sizes[c] = r.count;

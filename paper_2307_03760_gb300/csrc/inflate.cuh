@@ -410,7 +410,12 @@ __device__ int32_t inflate_decode(Ring& ring, uint8_t* scratch, int64_t n_in64,
         for (uint32_t k0 = 0; k0 < len; k0 += GPIECE) {
           const uint32_t piece = len - k0 < GPIECE ? len - k0 : GPIECE;
           if (!ring.ensure(src + k0, src + k0 + piece + 8)) return ST_TIMEOUT;
-          for (uint32_t k = lane; k < piece; k += 32) out[wpos + k0 + k] = ring.byte(src + k0 + k);
+          // every lane reads in every step (a register ring reads by shuffles)
+          for (uint32_t kb = 0; kb < piece; kb += 32) {
+            const uint32_t k = kb + lane;
+            const uint8_t v = ring.byte(src + k0 + (k < piece ? k : piece - 1));
+            if (k < piece) out[wpos + k0 + k] = v;
+          }
         }
         __syncwarp();
       } else if (STORE) {

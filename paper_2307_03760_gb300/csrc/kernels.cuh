@@ -26,12 +26,17 @@ using DeflateRing = InRing<256, 4>;
 constexpr int kLitTB = 10, kDistTB = 8, kWin = 0;
 using DeflateSmem = InflateSmem<kLitTB, kDistTB, kWin>;
 
-constexpr int round128(int x) { return (x + 127) & ~127; }
+__host__ __device__ constexpr int round128(int x) { return (x + 127) & ~127; }
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 constexpr int kRleV1Warp = round128(RleRing::SMEM + kRleV1Scratch);
 constexpr int kRleV2Warp = round128(RleRing::SMEM + kRleV2Scratch);
 constexpr int kDeflateWarp = round128(DeflateRing::SMEM + DeflateSmem::BYTES);
+// per-warp shared memory of a one-warp-per-chunk kernel: input ring + scratch
+// (Deflate tables for Deflate and ORC zlib streams; none for byte RLE)
+__host__ __device__ constexpr int warp_chunk_smem(int family, int ring_smem) {
+  return round128(ring_smem + (family == 4 ? 0 : DeflateSmem::BYTES));
+}
 // per-warp scratch of the RLE decoders besides their input
 constexpr int kRleScratch = 512;
 // plain RLE kernels: whole-chunk staging area per CTA (chunks up to about
@@ -107,6 +112,8 @@ __host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
 __global__ void orc_zlib_kernel(Args a);
 __global__ void orc_zlib_sizes_kernel(Args a);
 __global__ void byte_rle_kernel(Args a);
+__global__ void byte_rle_reg_kernel(Args a);
+__global__ void inflate_reg_kernel(Args a);
 __global__ void byte_rle_sizes_kernel(Args a);
 __global__ void rle_v1_kernel(Args a);
 __global__ void rle_v1_sizes_kernel(Args a);

@@ -13,6 +13,13 @@ __global__ void __launch_bounds__(kThreads) orc_zlib_sizes_kernel(Args a) {
   warp_chunk_body<5, false>(a);
 }
 __global__ void __launch_bounds__(kThreads) byte_rle_kernel(Args a) { warp_chunk_body<4, true>(a); }
+// the same decoders with the register staging ring (no shared-memory input)
+__global__ void __launch_bounds__(kThreads, 10) inflate_reg_kernel(Args a) {
+  warp_chunk_body<3, true, RegRing>(a);
+}
+__global__ void __launch_bounds__(kThreads) byte_rle_reg_kernel(Args a) {
+  warp_chunk_body<4, true, RegRing>(a);
+}
 __global__ void __launch_bounds__(kThreads) byte_rle_sizes_kernel(Args a) {
   warp_chunk_body<4, false>(a);
 }

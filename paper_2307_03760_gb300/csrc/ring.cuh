@@ -158,6 +158,79 @@ struct InRing {
   }
 };
 
+// Register staging ring (CODAG Sec. V-E, the register input buffer): the
+// warp keeps a 512-byte window of the chunk in registers, 8 bytes per lane in
+// each of two 256-byte halves, plus the next 256 bytes already requested;
+// ensure() slides the window forward by halves.  A read takes its bytes from
+// the lane that holds them (__shfl_sync), so it needs no shared memory; every
+// lane keeps the same window state.  Positions and the readable range are
+// those of InRing; an ensure() span must not exceed MAX_SPAN.  Every read is
+// a warp-wide shuffle, so all 32 lanes must make each read together (a lane
+// may ask for a different position than the others); decoders that use it
+// keep their per-lane loops at a warp-uniform trip count.
+struct RegRing {
+  static constexpr int HALF = 256;
+  static constexpr int MAX_SPAN = HALF;
+  static constexpr int SMEM = 0;
+  const uint8_t* gsrc;  // 16-byte aligned global address of ring position 0
+  int64_t skew;         // chunk start - gsrc
+  int64_t limit;        // readable ring positions: [0, limit)
+  int64_t base;         // ring position of the window start (a multiple of HALF)
+  uint64_t h0, h1, nx;  // this lane's 8 bytes of the two halves and the next one
+
+  __device__ __forceinline__ void init(uint8_t*) {}
+  // 8 bytes at ring position r (a multiple of 8); bytes past the readable
+  // range read as zero
+  __device__ __forceinline__ uint64_t fetch(int64_t r) const {
+    if (r + 8 <= limit) return __ldg(reinterpret_cast<const unsigned long long*>(gsrc + r));
+    uint64_t v = 0;
+    for (int k = 0; k < 8; k++)
+      if (r + k < limit) v |= (uint64_t)__ldg(gsrc + r + k) << (8 * k);
+    return v;
+  }
+  __device__ __forceinline__ void start(const uint8_t* chunk, int64_t, const uint8_t* buf_end) {
+    gsrc = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(chunk) & ~uintptr_t(15));
+    skew = chunk - gsrc;
+    limit = buf_end - gsrc;
+    base = 0;
+    const int64_t l8 = 8 * (int64_t)lane_id();
+    h0 = fetch(l8);
+    h1 = fetch(HALF + l8);
+    nx = fetch(2 * HALF + l8);
+  }
+  __device__ __forceinline__ bool ensure(int64_t lo, int64_t hi) {
+    hi += skew;
+    while (hi > base + 2 * HALF) {
+      h0 = h1;
+      h1 = nx;
+      base += HALF;
+      nx = fetch(base + 2 * HALF + 8 * (int64_t)lane_id());
+    }
+    return lo + skew >= base;
+  }
+  __device__ __forceinline__ bool drain() { return true; }
+  __device__ __forceinline__ const uint8_t* chunk_ptr() const { return gsrc + skew; }
+  // the 8 bytes at ring position r (a multiple of 8 inside the window)
+  __device__ __forceinline__ uint64_t word(int64_t r) const {
+    const uint32_t o = (uint32_t)(r - base);
+    const int src = (int)((o >> 3) & 31);
+    const uint64_t a = shfl64(h0, src), b = shfl64(h1, src);
+    return o >= (uint32_t)HALF ? b : a;
+  }
+  __device__ __forceinline__ uint8_t byte(int64_t p) const {
+    const int64_t r = p + skew;
+    return (uint8_t)(word(r & ~int64_t(7)) >> (8 * (uint32_t)(r & 7)));
+  }
+  __device__ __forceinline__ uint64_t u64(int64_t p) const {
+    const int64_t r = p + skew;
+    const int64_t a = r & ~int64_t(7);
+    const uint32_t sh = 8 * (uint32_t)(r & 7);
+    const uint64_t w0 = word(a), w1 = word(a + 8);
+    return sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
+  }
+  __device__ __forceinline__ uint32_t u32(uint32_t p) const { return (uint32_t)u64(p); }
+};
+
 // Input that is wholly resident in shared memory: a CTA stages a whole
 // compressed chunk at once (TMA bulk copies on one mbarrier) and its warps
 // read it with the same interface as the ring, without further waits.

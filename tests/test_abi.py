@@ -83,6 +83,18 @@ def test_host_entry_argument_errors_without_gpu():
     assert b"non-decreasing" in L.codag_last_error()
 
 
+def test_input_staging_setting():
+    L = codag.lib()
+    assert L.codag_set_input_staging(1, 1) == codag.CODAG_EINVAL  # RLE v1 always stages in smem
+    assert L.codag_set_input_staging(3, 2) == codag.CODAG_EINVAL
+    assert L.codag_get_input_staging(2) == -1
+    for f in (3, 6, 7):
+        assert L.codag_set_input_staging(f, 1) == codag.CODAG_OK
+        assert L.codag_get_input_staging(f) == 1
+        assert L.codag_set_input_staging(f, 0) == codag.CODAG_OK
+        assert L.codag_get_input_staging(f) == 0
+
+
 def test_python_binding_names_match_abi():
     for name in declared_functions():
         if name in ("codag_last_error",):
