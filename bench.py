@@ -494,6 +494,10 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
         w = workload(name, 1)
         d = Dev(w, torch, dev)
         fmt = FMT_OF[name]
+        if name in ("rle_v1", "rle_v2"):  # this family's tuned warps per chunk (auto if none)
+            from paper_2307_03760_gb300 import autotune
+            codag.codag_set_parts_per_chunk(0)
+            autotune.apply(n_chunks=w.n, family=name)
         args = (fmt, d.comp.data_ptr(), d.coff.data_ptr(), w.n, d.out.data_ptr(), d.ooff.data_ptr())
         sh = stream.cuda_stream
         fn = lambda: codag.codag_decompress(*args, stream=sh)  # noqa: E731
@@ -507,6 +511,7 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
                      "ms": round(t, 4), "chunks": w.n, "ratio": round(w.comp_bytes / w.out_bytes, 4),
                      "all_ok": bool((st == 0).all()), "workload": WORKLOAD_DESC[name]}
         del d
+    codag.codag_set_parts_per_chunk(0)
     # mixed batch: persistent graph-captured launch vs one plain launch per format
     w = workload("batched", 1)
     d = Dev(w, torch, dev)
@@ -516,9 +521,19 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
     parts = split_by_format(w)
     devs = {f: Dev(p, torch, dev) for f, p in parts.items()}
 
+    # each plain launch with its family's tuned warps per chunk
+    from paper_2307_03760_gb300 import autotune
+    tuned_parts = {}
+    if os.path.exists(autotune.DEFAULT_TABLE):
+        with open(autotune.DEFAULT_TABLE) as fh:
+            rp = json.load(fh).get("rle_parts", {})
+        tuned_parts = {1: rp.get("rle_v1", {}).get("best", 0), 2: rp.get("rle_v2", {}).get("best", 0)}
+
     def three():
         for f, pd in devs.items():
+            codag.codag_set_parts_per_chunk(int(tuned_parts.get(f, 0)))
             codag.codag_decompress(f, pd.comp, pd.coff, pd.w.n, pd.out, pd.ooff)
+        codag.codag_set_parts_per_chunk(0)
 
     ms_p = time_steps(torch, stream, three, 10, 3)
     tg, tp = statistics.median(ms_g), statistics.median(ms_p)

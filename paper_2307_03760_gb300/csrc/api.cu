@@ -81,8 +81,8 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
-                 {(const void*)byte_rle_kernel, kWarpsPerBlock * warp_chunk_smem(4, DeflateRing::SMEM)},
-                 {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, DeflateRing::SMEM)},
+                 {(const void*)byte_rle_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
+                 {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
                  {(const void*)batch_kernel, kBatchSmem}};
     for (auto& at : attrs) {
@@ -201,7 +201,8 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     // decode kernels of Deflate and byte / boolean RLE may stage their input
     // in registers instead of a shared-memory ring (codag_set_input_staging)
     const bool reg = store && (fam == 3 || fam == 4) && g_reg_ring[fam].load() == 1;
-    smem = (size_t)kWarpsPerBlock * warp_chunk_smem(fam == 5 ? 3 : fam, reg ? 0 : DeflateRing::SMEM);
+    const int ring_smem = reg ? 0 : fam == 4 ? RleRing::SMEM : DeflateRing::SMEM;
+    smem = (size_t)kWarpsPerBlock * warp_chunk_smem(fam == 5 ? 3 : fam, ring_smem);
     if (fam == 3)
       fn = !store ? (const void*)inflate_sizes_kernel : reg ? (const void*)inflate_reg_kernel : (const void*)inflate_kernel;
     else if (fam == 4)

@@ -12,7 +12,9 @@ __global__ void __launch_bounds__(kThreads, 10) orc_zlib_kernel(Args a) { warp_c
 __global__ void __launch_bounds__(kThreads) orc_zlib_sizes_kernel(Args a) {
   warp_chunk_body<5, false>(a);
 }
-__global__ void __launch_bounds__(kThreads) byte_rle_kernel(Args a) { warp_chunk_body<4, true>(a); }
+// byte RLE consumes its input about ten times faster per instruction than
+// Deflate: it stages through the 4 KiB ring, so that refills run well ahead
+__global__ void __launch_bounds__(kThreads) byte_rle_kernel(Args a) { warp_chunk_body<4, true, RleRing>(a); }
 // the same decoders with the register staging ring (no shared-memory input)
 __global__ void __launch_bounds__(kThreads, 10) inflate_reg_kernel(Args a) {
   warp_chunk_body<3, true, RegRing>(a);
@@ -21,7 +23,7 @@ __global__ void __launch_bounds__(kThreads) byte_rle_reg_kernel(Args a) {
   warp_chunk_body<4, true, RegRing>(a);
 }
 __global__ void __launch_bounds__(kThreads) byte_rle_sizes_kernel(Args a) {
-  warp_chunk_body<4, false>(a);
+  warp_chunk_body<4, false, RleRing>(a);
 }
 
 }  // namespace codag

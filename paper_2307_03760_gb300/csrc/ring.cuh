@@ -280,6 +280,19 @@ struct OffsetRing : OffsetIn<Ring> {
   static constexpr int MAX_SPAN = Ring::MAX_SPAN;
 };
 
+// Inputs whose every chunk byte is resident in shared memory (any position
+// can be read at any time, without ensure()).
+template <class In>
+struct resident_input {
+  static constexpr bool value = false;
+};
+template <>
+struct resident_input<StagedInput> {
+  static constexpr bool value = true;
+};
+template <class In>
+struct resident_input<OffsetIn<In>> : resident_input<In> {};
+
 // Bytes a staged chunk of n_in bytes needs: 16-byte alignment skew in front,
 // and reads of up to 16 bytes past the last position (stale but in bounds).
 __host__ __device__ __forceinline__ int64_t staged_bytes(int64_t n_in) { return n_in + 15 + 32; }

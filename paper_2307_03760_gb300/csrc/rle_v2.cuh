@@ -269,7 +269,9 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
         uint64_t x = 0;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-          const uint64_t b = at + k < n_in ? (uint64_t)__ldg(src + at + k) : 0ull;
+          // a chunk staged whole is read in shared memory, a ring's in global
+          uint64_t b = 0;
+          if (at + k < n_in) b = resident_input<In>::value ? (uint64_t)in.byte(at + k) : (uint64_t)__ldg(src + at + k);
           x = (x << 8) | b;
         }
         const uint64_t e = (x << (bit & 7)) >> (64 - r.ew);
@@ -357,17 +359,32 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
             if (lane == 1) o[1] = basev + delta;
             uint64_t carry = basev + delta;
             const uint32_t nd = len - 2;
-            if (w <= 26) {  // 32 deltas of <= 26 bits sum below 2^31: 32-bit scan
+            if (w <= 26) {  // 32 deltas of <= 26 bits sum below 2^31: 32-bit scans
               if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
               const uint32_t sec32 = (uint32_t)r.sec;
+              const uint32_t step = 32u * (uint32_t)w;
               uint32_t bit = lane * (uint32_t)w;
-              for (uint32_t j0 = 0; j0 < nd; j0 += 32, bit += 32u * (uint32_t)w) {
+              uint32_t j0 = 0;
+              // 64 deltas per step: two independent scans, so their shuffle
+              // chains overlap; only the carry links the steps
+              for (; j0 + 32 < nd; j0 += 64, bit += 2 * step) {
+                const uint32_t ja = j0 + lane, jb = ja + 32;
+                const uint32_t da = v2_unpack32(in, sec32, bit, w);
+                const uint32_t db = jb < nd ? v2_unpack32(in, sec32, bit + step, w) : 0u;
+                const uint32_t sa = warp_incl_scan32(da);
+                const uint32_t sb = warp_incl_scan32(db);
+                const uint64_t ta = __shfl_sync(FULL, sa, 31);
+                const uint64_t tb = __shfl_sync(FULL, sb, 31);
+                const uint64_t cb = negative ? carry - ta : carry + ta;
+                o[2 + ja] = negative ? carry - (uint64_t)sa : carry + (uint64_t)sa;
+                if (jb < nd) o[2 + jb] = negative ? cb - (uint64_t)sb : cb + (uint64_t)sb;
+                carry = negative ? cb - tb : cb + tb;
+              }
+              if (j0 < nd) {  // the last 1..32 deltas
                 const uint32_t j = j0 + lane;
                 const uint32_t d = j < nd ? v2_unpack32(in, sec32, bit, w) : 0u;
                 const uint32_t sc = warp_incl_scan32(d);
-                const uint64_t s = negative ? carry - (uint64_t)sc : carry + (uint64_t)sc;
-                if (j < nd) o[2 + j] = s;
-                carry = shfl64(s, 31);
+                if (j < nd) o[2 + j] = negative ? carry - (uint64_t)sc : carry + (uint64_t)sc;
               }
             } else {
               for (uint32_t j0 = 0; j0 < nd; j0 += 32) {
