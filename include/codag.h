@@ -279,12 +279,14 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm);
 int codag_get_batch_ctas_per_sm(void);
 
 /*
- * Parts per chunk for the plain RLE calls (codag_decompress with an RLE
- * format): one CTA per chunk runs this many warps, each decoding the runs
- * that start in its share of the chunk's output values (every warp walks the
- * run headers before its share).  0 = automatic (the default: the smallest
- * power of two that gives at least 32 warps per SM, at most 16); otherwise a
- * power of two <= 16.  Used by the autotuner.
+ * Warps per chunk for the plain RLE calls (codag_decompress with an RLE
+ * format): one CTA per chunk runs this many warps.  A chunk staged whole in
+ * shared memory is cut into segments of about 1024 values (256 for RLE v1):
+ * one warp walks the run headers and publishes where each segment starts,
+ * and every warp claims segments and decodes them; a larger chunk is cut
+ * into one part per warp.  0 = automatic (the default: the smallest power of
+ * two that gives at least 32 warps per SM, at most 16); otherwise 1..16.
+ * Used by the autotuner.
  */
 codag_status codag_set_parts_per_chunk(int parts);
 int codag_get_parts_per_chunk(void);

@@ -77,7 +77,7 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1) -> dict:
         comp, coff, ooff, _, out, _ = upload(w)
         fmt = int(w.formats[0])
         run = lambda: codag.codag_decompress(fmt, comp, coff, w.n, out, ooff)  # noqa: E731
-        t = sweep(run, [1, 2, 4, 8, 16], codag.codag_set_parts_per_chunk, timer=timer)
+        t = sweep(run, list(range(1, 17)), codag.codag_set_parts_per_chunk, timer=timer)
         best, ms = choose(t)
         table["rle_parts"][name] = {"chunks": w.n, "best": best, "ms": round(ms, 4)}
         table["sweeps"][f"{name}_parts"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}

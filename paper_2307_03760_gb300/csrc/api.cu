@@ -603,8 +603,7 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm) {
 int codag_get_batch_ctas_per_sm(void) { return g_batch_ctas_per_sm.load(); }
 
 codag_status codag_set_parts_per_chunk(int parts) {
-  if (parts < 0 || parts > 16 || (parts & (parts - 1)))
-    return fail(CODAG_EINVAL, "parts per chunk must be 0 or a power of two <= 16");
+  if (parts < 0 || parts > 16) return fail(CODAG_EINVAL, "parts per chunk must be 0..16");
   g_parts_per_chunk.store(parts);
   return CODAG_OK;
 }

@@ -514,7 +514,9 @@ __device__ PartResult rle_v1_part(In& in, uint16_t* ends, int64_t n_in, bool is_
       uint64_t* o = out + count;
       if (!gr.literal) {
         const uint64_t base = is_signed ? unzigzag(gr.base) : gr.base;
-        for (uint32_t i = lane; i < gr.len; i += 32) o[i] = base + (uint64_t)i * (uint64_t)gr.delta;
+        uint64_t v = base + (uint64_t)lane * (uint64_t)gr.delta;  // value i = base + i * delta
+        const uint64_t step = 32ull * (uint64_t)gr.delta;
+        for (uint32_t i = lane; i < gr.len; i += 32, v += step) o[i] = v;
       } else {
         for (int j = (int)lane; j < (int)gr.len; j += 32) {  // lane j decodes varint j
           const int s = j == 0 ? 0 : ends[j - 1] + 1;

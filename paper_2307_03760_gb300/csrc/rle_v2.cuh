@@ -330,8 +330,16 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
           if (w <= 25) {  // whole run resident at once (<= 1600 bytes), 32-bit unpack
             if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
             const uint32_t sec32 = (uint32_t)r.sec;
+            const uint32_t step = 32u * (uint32_t)w;
             uint32_t bit = lane * (uint32_t)w;
-            for (uint32_t i = lane; i < len; i += 32, bit += 32u * (uint32_t)w) {
+            uint32_t i = lane;
+            for (; i + 32 < len; i += 64, bit += 2 * step) {  // two values per lane and step
+              const uint32_t va = v2_unpack32(in, sec32, bit, w);
+              const uint32_t vb = v2_unpack32(in, sec32, bit + step, w);
+              o[i] = is_signed ? unzigzag32(va) : (uint64_t)va;
+              o[i + 32] = is_signed ? unzigzag32(vb) : (uint64_t)vb;
+            }
+            if (i < len) {
               const uint32_t v = v2_unpack32(in, sec32, bit, w);
               o[i] = is_signed ? unzigzag32(v) : (uint64_t)v;
             }
@@ -351,8 +359,10 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
           uint64_t basev = r.basev;
           if (is_signed) basev = unzigzag(basev);
           const uint64_t delta = unzigzag(r.dz);
-          if (w == 0 || len < 3) {
-            for (uint32_t i = lane; i < len; i += 32) o[i] = basev + (uint64_t)i * delta;
+          if (w == 0 || len < 3) {  // value i = base + i * delta, as a running sum
+            uint64_t v = basev + (uint64_t)lane * delta;
+            const uint64_t step = 32ull * delta;
+            for (uint32_t i = lane; i < len; i += 32, v += step) o[i] = v;
           } else {
             const bool negative = (int64_t)delta < 0;
             if (lane == 0) o[0] = basev;

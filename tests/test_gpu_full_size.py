@@ -20,10 +20,21 @@ THREADS = os.cpu_count() or 4
 
 @pytest.mark.parametrize("name", ["rle_v1", "rle_v2", "deflate"])
 def test_full_column(name):
+    """In the launch configuration the benchmark times: the committed
+    autotuner table applied for this family."""
+    import paper_2307_03760_gb300 as codag
+    from paper_2307_03760_gb300 import autotune
     w = {"rle_v1": synth.rle_v1_column, "rle_v2": synth.rle_v2_column,
          "deflate": synth.deflate_column}[name](seed=1)
     fmt = int(w.formats[0])
-    got, st = run_plain(fmt, w.comp, w.comp_off, w.out_off)
+    autotune.apply(n_chunks=None, family=name)
+    try:
+        got, st = run_plain(fmt, w.comp, w.comp_off, w.out_off)
+    finally:
+        codag.codag_set_parts_per_chunk(0)
+        codag.codag_set_batch_ctas_per_sm(0)
+        for f in (3, 6, 7):
+            codag.codag_set_input_staging(f, 0)
     assert (st == 0).all()
     assert_parity(fmt, w.comp, w.comp_off, w.out_off, got, st, threads=THREADS)
 

@@ -123,7 +123,7 @@ def test_short_streams_exhaustive(fmt):
     assert (gsz[sst == 0] == sz[sst == 0]).all()
 
 
-@pytest.fixture(params=[0, 1, 16], ids=["parts_auto", "parts_1", "parts_16"])
+@pytest.fixture(params=[0, 1, 6, 16], ids=["parts_auto", "parts_1", "parts_6", "parts_16"])
 def parts(request):
     """Plain RLE calls split every chunk into this many warp-decoded parts."""
     import paper_2307_03760_gb300 as codag
