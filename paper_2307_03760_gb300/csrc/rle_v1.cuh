@@ -90,12 +90,14 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t r) {
   return pos + ((r > (w & 1u)) ? 1u : 0u);
 }
 
-// Decode the low 7-bit groups of an 8-byte window (byte k -> bits 7k..7k+6).
+// Decode the low 7-bit groups of an 8-byte window (byte k -> bits 7k..7k+6):
+// drop the stop bits, then close the gaps pairwise, 7-bit groups into
+// 14-bit, 14 into 28, 28 into 56, in three shift-and-merge steps.
 __device__ __forceinline__ uint64_t varint_compact8(uint64_t x) {
-  return (x & 0x7full) | ((x >> 1) & (0x7full << 7)) | ((x >> 2) & (0x7full << 14)) |
-         ((x >> 3) & (0x7full << 21)) | ((x >> 4) & (0x7full << 28)) |
-         ((x >> 5) & (0x7full << 35)) | ((x >> 6) & (0x7full << 42)) |
-         ((x >> 7) & (0x7full << 49));
+  x &= 0x7f7f7f7f7f7f7f7full;
+  x = (x & 0x007f007f007f007full) | ((x & 0x7f007f007f007f00ull) >> 1);
+  x = (x & 0x00003fff00003fffull) | ((x & 0x3fff00003fff0000ull) >> 2);
+  return (x & 0x000000000fffffffull) | ((x & 0x0fffffff00000000ull) >> 4);
 }
 
 // Varint at chunk position p (bytes resident through p+16).  Returns a status;

@@ -265,24 +265,27 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
       if ((int)lane < r.pll) {
         const uint64_t bit = (uint64_t)lane * (uint64_t)r.ew;
         const int64_t at = r.psec + (int64_t)(bit >> 3);
-        const uint8_t* src = in.chunk_ptr();
         uint64_t x = 0;
+        if (resident_input<In>::value) {  // a chunk staged whole: one 8-byte read in shared memory
+          x = bswap64(in.u64(at));
+          if (n_in - at < 8) x &= ~0ull << (8 * (uint32_t)(8 - (n_in - at)));  // bytes past the chunk: 0
+        } else {  // a ring only moves forward: the entries come from global memory
+          const uint8_t* src = in.chunk_ptr();
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          // a chunk staged whole is read in shared memory, a ring's in global
-          uint64_t b = 0;
-          if (at + k < n_in) b = resident_input<In>::value ? (uint64_t)in.byte(at + k) : (uint64_t)__ldg(src + at + k);
-          x = (x << 8) | b;
+          for (int k = 0; k < 8; k++) x = (x << 8) | (at + k < n_in ? (uint64_t)__ldg(src + at + k) : 0ull);
         }
         const uint64_t e = (x << (bit & 7)) >> (64 - r.ew);
         gap = e >> r.pw;  // pw <= 63 here
         patch = e & lowmask64(r.pw);
       }
       const bool real = (int)lane < r.pll && !(gap == 255 && patch == 0);
-      const uint64_t ppos = warp_incl_scan64(gap);
+      // positions as a 32-bit scan: a gap above 0xffff (only in a malformed
+      // entry) is clamped, which keeps its position and every later one at or
+      // past the run length, so the stream is rejected as with exact sums
+      const uint32_t ppos = warp_incl_scan32(gap > 0xffffull ? 0xffffu : (uint32_t)gap);
       const uint32_t before = __ballot_sync(FULL, real) & lanemask_lt();
       const int prev = before ? 31 - __clz(before) : 0;
-      const uint64_t prev_pos = shfl64(ppos, prev);
+      const uint32_t prev_pos = __shfl_sync(FULL, ppos, prev);
       const bool bad = real && (ppos >= len || (before != 0 && ppos <= prev_pos));
       if (__ballot_sync(FULL, bad)) return part_error(ST_BAD_HEADER, pos, count);
       if (count > cap_values || len > cap_values - count) return part_error(ST_OVERFLOW, pos, count);
