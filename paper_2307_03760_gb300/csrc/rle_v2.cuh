@@ -372,32 +372,37 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
             if (lane == 1) o[1] = basev + delta;
             uint64_t carry = basev + delta;
             const uint32_t nd = len - 2;
-            if (w <= 26) {  // 32 deltas of <= 26 bits sum below 2^31: 32-bit scans
+            if (w <= 26) {  // deltas of <= 26 bits: 64 of them sum below 2^32
               if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
               const uint32_t sec32 = (uint32_t)r.sec;
-              const uint32_t step = 32u * (uint32_t)w;
-              uint32_t bit = lane * (uint32_t)w;
+              uint64_t* od = o + 2;  // value j of the prefix-summed part
               uint32_t j0 = 0;
-              // 64 deltas per step: two independent scans, so their shuffle
-              // chains overlap; only the carry links the steps
-              for (; j0 + 32 < nd; j0 += 64, bit += 2 * step) {
-                const uint32_t ja = j0 + lane, jb = ja + 32;
-                const uint32_t da = v2_unpack32(in, sec32, bit, w);
-                const uint32_t db = jb < nd ? v2_unpack32(in, sec32, bit + step, w) : 0u;
-                const uint32_t sa = warp_incl_scan32(da);
-                const uint32_t sb = warp_incl_scan32(db);
-                const uint64_t ta = __shfl_sync(FULL, sa, 31);
-                const uint64_t tb = __shfl_sync(FULL, sb, 31);
-                const uint64_t cb = negative ? carry - ta : carry + ta;
-                o[2 + ja] = negative ? carry - (uint64_t)sa : carry + (uint64_t)sa;
-                if (jb < nd) o[2 + jb] = negative ? cb - (uint64_t)sb : cb + (uint64_t)sb;
-                carry = negative ? cb - tb : cb + tb;
+              // Lane i takes deltas j0 + 2i and j0 + 2i + 1 (one 8-byte read), so
+              // one 32-value scan covers 64 deltas and each lane stores both
+              // values with one 16-byte store; the first delta goes alone when
+              // that keeps the pairs 16-byte aligned.
+              if (reinterpret_cast<uintptr_t>(od) & 8) {
+                const uint32_t d = v2_unpack32(in, sec32, 0, w);
+                carry = negative ? carry - (uint64_t)d : carry + (uint64_t)d;
+                if (lane == 0) od[0] = carry;
+                j0 = 1;
               }
-              if (j0 < nd) {  // the last 1..32 deltas
-                const uint32_t j = j0 + lane;
-                const uint32_t d = j < nd ? v2_unpack32(in, sec32, bit, w) : 0u;
-                const uint32_t sc = warp_incl_scan32(d);
-                if (j < nd) o[2 + j] = negative ? carry - (uint64_t)sc : carry + (uint64_t)sc;
+              for (; j0 < nd; j0 += 64) {
+                const uint32_t j = j0 + 2 * lane;
+                uint32_t da = 0, db = 0;
+                if (j < nd) {
+                  const uint32_t b = j * (uint32_t)w;
+                  const uint64_t x = bswap64(in.u64(sec32 + (b >> 3))) << (b & 7);
+                  da = (uint32_t)(x >> (64 - w));
+                  if (j + 1 < nd) db = (uint32_t)((x << w) >> (64 - w));
+                }
+                const uint32_t incl = warp_incl_scan32(da + db);
+                const uint64_t s1 = negative ? carry - (uint64_t)(incl - db) : carry + (uint64_t)(incl - db);
+                const uint64_t s2 = negative ? carry - (uint64_t)incl : carry + (uint64_t)incl;
+                if (j + 1 < nd) *reinterpret_cast<ulonglong2*>(od + j) = make_ulonglong2(s1, s2);
+                else if (j < nd) od[j] = s1;
+                const uint64_t tot = __shfl_sync(FULL, incl, 31);
+                carry = negative ? carry - tot : carry + tot;
               }
             } else {
               for (uint32_t j0 = 0; j0 < nd; j0 += 32) {
