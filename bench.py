@@ -494,10 +494,10 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
         w = workload(name, 1)
         d = Dev(w, torch, dev)
         fmt = FMT_OF[name]
-        if name in ("rle_v1", "rle_v2"):  # this family's tuned warps per chunk (auto if none)
-            from paper_2307_03760_gb300 import autotune
-            codag.codag_set_parts_per_chunk(0)
-            autotune.apply(n_chunks=w.n, family=name)
+        # this family's tuned warps per chunk (auto if none)
+        from paper_2307_03760_gb300 import autotune
+        codag.codag_set_parts_per_chunk(0)
+        autotune.apply(n_chunks=w.n, family="byte_rle" if name == "bool_rle" else name)
         args = (fmt, d.comp.data_ptr(), d.coff.data_ptr(), w.n, d.out.data_ptr(), d.ooff.data_ptr())
         sh = stream.cuda_stream
         fn = lambda: codag.codag_decompress(*args, stream=sh)  # noqa: E731

@@ -73,7 +73,8 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1) -> dict:
                 torch.zeros(max(w.n, 1), dtype=torch.int32, device=dev))
 
     table = {"device": torch.cuda.get_device_name(0), "rle_parts": {}, "sweeps": {}}
-    for name, w in (("rle_v1", synth.rle_v1_column(seed)), ("rle_v2", synth.rle_v2_column(seed))):
+    for name, w in (("rle_v1", synth.rle_v1_column(seed)), ("rle_v2", synth.rle_v2_column(seed)),
+                    ("byte_rle", synth.byte_rle_column(seed))):
         comp, coff, ooff, _, out, _ = upload(w)
         fmt = int(w.formats[0])
         run = lambda: codag.codag_decompress(fmt, comp, coff, w.n, out, ooff)  # noqa: E731

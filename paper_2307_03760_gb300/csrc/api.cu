@@ -77,6 +77,7 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)rle_v1_sizes_kernel, kRleMaxSmem},
                  {(const void*)rle_v2_kernel, kRleMaxSmem},
                  {(const void*)rle_v2_sizes_kernel, kRleMaxSmem},
+                 {(const void*)byte_rle_cta_kernel, kRleMaxSmem},
                  {(const void*)inflate_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_kernel, kWarpsPerBlock * kDeflateWarp},
@@ -195,12 +196,13 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   const void* fn;
   unsigned grid, block;
   size_t smem;
-  if (fam >= 3) {
+  // decode kernels of Deflate and byte / boolean RLE may stage their input
+  // in registers instead of a shared-memory ring (codag_set_input_staging);
+  // byte / boolean RLE then runs a warp per chunk, else a CTA per chunk
+  const bool reg = store && (fam == 3 || fam == 4) && g_reg_ring[fam].load() == 1;
+  if (fam == 3 || fam == 5 || (fam == 4 && (!store || reg))) {
     grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     block = kThreads;
-    // decode kernels of Deflate and byte / boolean RLE may stage their input
-    // in registers instead of a shared-memory ring (codag_set_input_staging)
-    const bool reg = store && (fam == 3 || fam == 4) && g_reg_ring[fam].load() == 1;
     const int ring_smem = reg ? 0 : fam == 4 ? RleRing::SMEM : DeflateRing::SMEM;
     smem = (size_t)kWarpsPerBlock * warp_chunk_smem(fam == 5 ? 3 : fam, ring_smem);
     if (fam == 3)
@@ -225,6 +227,7 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
     if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);
     if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
+    else if (fam == 4) fn = (const void*)byte_rle_cta_kernel;
     else fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
   }
   void* params[] = {&a};

@@ -67,6 +67,11 @@ __device__ __forceinline__ PartResult decode_rle_part(In& in, uint8_t* scratch, 
   const uint64_t cap_v = g.cap / 8;
   PartResult r;
   vb.off += (uint32_t)base;
+  if (FAMILY == 4) {  // byte / boolean RLE: counts are decoded bytes (booleans)
+    r = byte_rle_part<STORE>(sub, g.n_in - base, format == FMT_BOOL_RLE, a.out + g.os, g.cap, count0, hi);
+    if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
+    return r;
+  }
   if (FAMILY == 1)
     r = rle_v1_part<STORE>(sub, reinterpret_cast<uint16_t*>(scratch), g.n_in - base,
                            format == FMT_RLE_V1_I64, out, cap_v, count0, hi, vb);
@@ -180,11 +185,13 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   const uint8_t* gsrc = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(chunk) & ~uintptr_t(15));
   const int64_t skew = chunk - gsrc;
   const bool staged = staged_bytes(g.n_in) <= stage_bytes;
-  const uint64_t cap_v = g.cap / 8;
+  // output units the segments split: values (RLE), decoded bytes (byte /
+  // boolean RLE)
+  const uint64_t cap_v = FAMILY != 4 ? g.cap / 8 : a.format == FMT_BOOL_RLE ? (g.cap + 7) / 8 : g.cap;
   // segments: about kSegValues values each, at least K, at most kMaxSeg
   uint32_t nseg = K;
   if (staged && STORE) {
-    const uint64_t want = cap_v / (FAMILY == 1 ? kSegValuesV1 : kSegValues);
+    const uint64_t want = cap_v / (FAMILY == 1 ? kSegValuesV1 : FAMILY == 4 ? kSegBytesByteRle : kSegValues);
     nseg = want < K ? K : want > (uint64_t)kMaxSeg ? (uint32_t)kMaxSeg : (uint32_t)want;
   }
   if (threadIdx.x == 0) {
@@ -251,6 +258,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
           rle_v1_walk_staged(in, bitmap, bitmap + rle_v1_bitmap_words(stage_bytes),
                              (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
                              published);
+        else if (FAMILY == 4)
+          byte_rle_walk(in, g.n_in, target, (int)nseg - 1, split_pos, split_cnt, published);
         else
           rle_v2_walk_staged(in, (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
                              published);
@@ -283,6 +292,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
       if (FAMILY == 1)
         rle_v1_walk(ring, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
                     split_pos, split_cnt);
+      else if (FAMILY == 4)
+        byte_rle_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
       else
         rle_v2_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
       ok = ring.drain();

@@ -46,6 +46,7 @@ constexpr int kRleStageBytes = 32768 + 256;
 constexpr int kMaxSeg = 64;
 constexpr int kSegValues = 1024;
 constexpr int kSegValuesV1 = 256;  // RLE v1: a cheap walk, so finer segments
+constexpr int kSegBytesByteRle = 4096;  // byte / boolean RLE: decoded bytes per segment
 // per-CTA extras: mbarrier, status key, published/claimed, split positions,
 // counts and targets
 constexpr int kRleCtaExtra = 24 + 3 * (kMaxSeg + 1) * 8;
@@ -112,6 +113,7 @@ __host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
 __global__ void orc_zlib_kernel(Args a);
 __global__ void orc_zlib_sizes_kernel(Args a);
 __global__ void byte_rle_kernel(Args a);
+__global__ void byte_rle_cta_kernel(Args a);
 __global__ void byte_rle_reg_kernel(Args a);
 __global__ void inflate_reg_kernel(Args a);
 __global__ void byte_rle_sizes_kernel(Args a);

@@ -9,6 +9,8 @@ __global__ void __launch_bounds__(512) rle_v1_sizes_kernel(Args a) {
   rle_cta_body<1, false>(a, a.stage_bytes);
 }
 __global__ void __launch_bounds__(512) rle_v2_kernel(Args a) { rle_cta_body<2, true>(a, a.stage_bytes); }
+// ORC byte / boolean RLE as a plain call: a CTA per chunk, like the above
+__global__ void __launch_bounds__(512) byte_rle_cta_kernel(Args a) { rle_cta_body<4, true>(a, a.stage_bytes); }
 __global__ void __launch_bounds__(512) rle_v2_sizes_kernel(Args a) {
   rle_cta_body<2, false>(a, a.stage_bytes);
 }
