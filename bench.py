@@ -377,8 +377,8 @@ def main():
     kernel_ms = statistics.mean(ms)  # one decode launch per step
     achieved = d.alg_bytes() / (kernel_ms / 1e3) / 1e9
     kernel = {"rle_v1": "rle_v1_kernel", "rle_v2": "rle_v2_kernel", "deflate": "inflate_kernel",
-              "batched": "batch_kernel", "byte_rle": "byte_rle_kernel",
-              "bool_rle": "byte_rle_kernel", "orc_zlib": "orc_zlib_kernel"}[name]
+              "batched": "batch_kernel", "byte_rle": "byte_rle_cta_kernel",
+              "bool_rle": "byte_rle_cta_kernel", "orc_zlib": "orc_zlib_kernel"}[name]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": traffic_from_profile(kernel, w.n), "kernel": kernel,
