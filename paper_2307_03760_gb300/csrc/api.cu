@@ -58,6 +58,12 @@ struct Workspace {
   uint32_t* counters = nullptr;  // kBatchCounterWords words
   bool attrs_set = false;
   int sm_count = 0;
+  int smem_per_sm = 0;     // shared memory per SM, bytes
+  int smem_reserved = 0;   // shared memory the system keeps per CTA
+  int smem_optin = 0;      // largest dynamic shared memory per CTA
+  // CTAs per SM that threads and registers allow for the CTA-per-chunk RLE
+  // kernels, by family (1, 2, 4) and warps per CTA (1..16); 0 = not known yet
+  mutable int rle_ctas[5][17] = {};
 };
 
 std::mutex g_mu;
@@ -73,11 +79,11 @@ codag_status current_ws(Workspace** out) {
     struct {
       const void* fn;
       int bytes;
-    } attrs[] = {{(const void*)rle_v1_kernel, kRleMaxSmem},
-                 {(const void*)rle_v1_sizes_kernel, kRleMaxSmem},
-                 {(const void*)rle_v2_kernel, kRleMaxSmem},
-                 {(const void*)rle_v2_sizes_kernel, kRleMaxSmem},
-                 {(const void*)byte_rle_cta_kernel, kRleMaxSmem},
+    } attrs[] = {{(const void*)rle_v1_kernel, -1},
+                 {(const void*)rle_v1_sizes_kernel, -1},
+                 {(const void*)rle_v2_kernel, -1},
+                 {(const void*)rle_v2_sizes_kernel, -1},
+                 {(const void*)byte_rle_cta_kernel, -1},
                  {(const void*)inflate_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)inflate_sizes_kernel, kWarpsPerBlock * kDeflateWarp},
                  {(const void*)orc_zlib_kernel, kWarpsPerBlock * kDeflateWarp},
@@ -86,12 +92,18 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
                  {(const void*)batch_kernel, kBatchSmem}};
+    e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (auto& at : attrs) {
-      e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, at.bytes);
+      // -1: a CTA-per-chunk RLE kernel, whose stage is sized at launch
+      // (rle_stage_bytes), up to the largest dynamic shared memory of a CTA
+      const int bytes = at.bytes >= 0 ? at.bytes : w.smem_optin > kRleMaxSmem ? w.smem_optin : kRleMaxSmem;
+      e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
-    e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     e = cudaMalloc(&w.counters, kBatchCounterWords * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(CODAG_ENOMEM, "workspace allocation failed");
     w.attrs_set = true;
@@ -176,6 +188,31 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
                        stream);
 }
 
+// Whole-chunk stage of a CTA-per-chunk RLE launch (family fam, `parts`
+// warps): at least kRleStageBytes (and room for the per-warp rings of the
+// fallback path), widened to all the shared memory that the CTAs per SM
+// allowed by threads and registers leave free, so that more chunks are
+// staged whole without costing occupancy.
+int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts) {
+  int stage = kRleStageBytes;
+  if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;
+  int& ctas = w.rle_ctas[fam][parts];
+  if (ctas == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 32 * parts, 0) != cudaSuccess) {
+    cudaGetLastError();
+    ctas = -1;
+  }
+  if (ctas <= 0 || w.smem_per_sm <= 0) return stage;
+  const int other = parts * kRleScratch + kRleCtaExtra;
+  int budget = w.smem_per_sm / ctas - w.smem_reserved;
+  if (budget > w.smem_optin) budget = w.smem_optin;
+  budget -= other;
+  // RLE v1 adds a terminator bitmap of about a quarter of the stage (+384 B)
+  int wide = fam == 1 ? (budget - 384) / 5 * 4 : budget;
+  wide &= ~255;
+  while (fam == 1 && wide > 0 && wide + rle_v1_bitmap_bytes(wide) > budget) wide -= 256;
+  return wide > stage ? wide : stage;
+}
+
 // One plain decode (or sizes) launch over chunks [0, n) of the given arrays,
 // statuses to `status`.  Arguments are checked and g_mu is held by the caller.
 codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
@@ -221,14 +258,13 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     }
     grid = (unsigned)n;
     block = 32u * (unsigned)parts;
-    int stage = kRleStageBytes;
-    if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;  // ring fallback fits
-    a.stage_bytes = stage;
-    smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
-    if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);
     if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
     else if (fam == 4) fn = (const void*)byte_rle_cta_kernel;
     else fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
+    const int stage = rle_stage_bytes(*w, fn, fam, parts);
+    a.stage_bytes = stage;
+    smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
+    if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);
   }
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, stream);

@@ -39,8 +39,8 @@ __host__ __device__ constexpr int warp_chunk_smem(int family, int ring_smem) {
 }
 // per-warp scratch of the RLE decoders besides their input
 constexpr int kRleScratch = 512;
-// plain RLE kernels: whole-chunk staging area per CTA (chunks up to about
-// 32 KiB compressed are staged in one piece) and the largest launch
+// plain RLE kernels: the smallest whole-chunk staging area per CTA (the
+// launch widens it to the shared memory that occupancy leaves free)
 constexpr int kRleStageBytes = 32768 + 256;
 // segments of a staged RLE chunk: about kSegValues values each, at most kMaxSeg
 constexpr int kMaxSeg = 64;

@@ -156,6 +156,25 @@ struct InRing {
     const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + ((a + 8) & (BYTES - 1)));
     return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
   }
+  // The same reads in big-endian byte order (byte p most significant): the
+  // unaligned shift and the byte swap are one byte permute per result word.
+  __device__ __forceinline__ uint32_t u32be(uint32_t p) const {
+    const uint32_t r = p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sel = 0x0123u + (r & 3u) * 0x1111u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + (a & (BYTES - 1)));
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + ((a + 4) & (BYTES - 1)));
+    return __byte_perm(w0, w1, sel);
+  }
+  __device__ __forceinline__ uint64_t u64be(int64_t p) const {
+    const uint32_t r = (uint32_t)p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sel = 0x0123u + (r & 3u) * 0x1111u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + (a & (BYTES - 1)));
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + ((a + 4) & (BYTES - 1)));
+    const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + ((a + 8) & (BYTES - 1)));
+    return ((uint64_t)__byte_perm(w0, w1, sel) << 32) | __byte_perm(w1, w2, sel);
+  }
 };
 
 // Register staging ring (CODAG Sec. V-E, the register input buffer): the
@@ -229,6 +248,8 @@ struct RegRing {
     return sh ? (w0 >> sh) | (w1 << (64 - sh)) : w0;
   }
   __device__ __forceinline__ uint32_t u32(uint32_t p) const { return (uint32_t)u64(p); }
+  __device__ __forceinline__ uint32_t u32be(uint32_t p) const { return bswap32(u32(p)); }
+  __device__ __forceinline__ uint64_t u64be(int64_t p) const { return bswap64(u64(p)); }
 };
 
 // Input that is wholly resident in shared memory: a CTA stages a whole
@@ -259,6 +280,24 @@ struct StagedInput {
     const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + a + 8);
     return ((uint64_t)__funnelshift_r(w1, w2, sh) << 32) | __funnelshift_r(w0, w1, sh);
   }
+  // big-endian, as for InRing
+  __device__ __forceinline__ uint32_t u32be(uint32_t p) const {
+    const uint32_t r = p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sel = 0x0123u + (r & 3u) * 0x1111u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + a);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + a + 4);
+    return __byte_perm(w0, w1, sel);
+  }
+  __device__ __forceinline__ uint64_t u64be(int64_t p) const {
+    const uint32_t r = (uint32_t)p + (uint32_t)skew;
+    const uint32_t a = r & ~3u;
+    const uint32_t sel = 0x0123u + (r & 3u) * 0x1111u;
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(buf + a);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(buf + a + 4);
+    const uint32_t w2 = *reinterpret_cast<const uint32_t*>(buf + a + 8);
+    return ((uint64_t)__byte_perm(w0, w1, sel) << 32) | __byte_perm(w1, w2, sel);
+  }
 };
 
 // View of an input shifted by `base` bytes: a part decoder reads its own
@@ -272,6 +311,8 @@ struct OffsetIn {
   __device__ __forceinline__ uint8_t byte(int64_t p) const { return in->byte(p + base); }
   __device__ __forceinline__ uint32_t u32(uint32_t p) const { return in->u32(p + (uint32_t)base); }
   __device__ __forceinline__ uint64_t u64(int64_t p) const { return in->u64(p + base); }
+  __device__ __forceinline__ uint32_t u32be(uint32_t p) const { return in->u32be(p + (uint32_t)base); }
+  __device__ __forceinline__ uint64_t u64be(int64_t p) const { return in->u64be(p + base); }
 };
 
 // The same view over a staging ring, for decoders that need the ring's span.
@@ -292,6 +333,12 @@ struct resident_input<StagedInput> {
 };
 template <class In>
 struct resident_input<OffsetIn<In>> : resident_input<In> {};
+
+// Big-endian 4- and 8-byte reads at chunk position p (MSB-first bit fields).
+template <class In>
+__device__ __forceinline__ uint32_t load_be32(const In& in, uint32_t p) { return in.u32be(p); }
+template <class In>
+__device__ __forceinline__ uint64_t load_be64(const In& in, int64_t p) { return in.u64be(p); }
 
 // Bytes a staged chunk of n_in bytes needs: 16-byte alignment skew in front,
 // and reads of up to 16 bytes past the last position (stale but in bounds).

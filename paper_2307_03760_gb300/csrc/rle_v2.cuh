@@ -43,15 +43,15 @@ __device__ __forceinline__ int v2_closest_fixed_bits(int n) {
 template <class Ring>
 __device__ __forceinline__ uint64_t v2_unpack(const Ring& ring, int64_t sec, uint64_t i, int w) {
   const uint64_t bit = i * (uint64_t)w;
-  const uint64_t x = bswap64(ring.u64(sec + (int64_t)(bit >> 3)));
+  const uint64_t x = load_be64(ring, sec + (int64_t)(bit >> 3));
   return (x << (bit & 7)) >> (64 - w);
 }
 
 // value at bit offset `bit` (width w <= 25) of a packed section at chunk
-// position sec: one unaligned 4-byte read, a byte swap and two 32-bit shifts
+// position sec: one unaligned big-endian 4-byte read and two 32-bit shifts
 template <class In>
 __device__ __forceinline__ uint32_t v2_unpack32(const In& in, uint32_t sec, uint32_t bit, int w) {
-  const uint32_t x = bswap32(in.u32(sec + (bit >> 3)));
+  const uint32_t x = load_be32(in, sec + (bit >> 3));
   return (x << (bit & 7)) >> (32 - w);
 }
 
@@ -255,7 +255,7 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
     const uint32_t len = r.len;
     const int w = r.w;
     if (r.enc == 2) {  // patch list validity belongs to the run's own checks
-      const uint64_t mag = bswap64(in.u64(pos + 4)) >> (64 - 8 * r.bw);
+      const uint64_t mag = load_be64(in, pos + 4) >> (64 - 8 * r.bw);
       const uint64_t sign = 1ull << (8 * r.bw - 1);
       const uint64_t base = (mag & sign) ? 0ull - (mag & ~sign) : mag;
       // one entry per lane, read straight from global memory (at most 31
@@ -267,7 +267,7 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
         const int64_t at = r.psec + (int64_t)(bit >> 3);
         uint64_t x = 0;
         if (resident_input<In>::value) {  // a chunk staged whole: one 8-byte read in shared memory
-          x = bswap64(in.u64(at));
+          x = load_be64(in, at);
           if (n_in - at < 8) x &= ~0ull << (8 * (uint32_t)(8 - (n_in - at)));  // bytes past the chunk: 0
         } else {  // a ring only moves forward: the entries come from global memory
           const uint8_t* src = in.chunk_ptr();
@@ -326,7 +326,7 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
       if (STORE) {
         uint64_t* o = out + count;
         if (r.enc == 0) {  // SHORT_REPEAT
-          uint64_t v = bswap64(in.u64(pos + 1)) >> (64 - 8 * w);
+          uint64_t v = load_be64(in, pos + 1) >> (64 - 8 * w);
           if (is_signed) v = unzigzag(v);
           if (lane < len) o[lane] = v;
         } else if (r.enc == 1) {  // DIRECT
@@ -392,7 +392,7 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
                 uint32_t da = 0, db = 0;
                 if (j < nd) {
                   const uint32_t b = j * (uint32_t)w;
-                  const uint64_t x = bswap64(in.u64(sec32 + (b >> 3))) << (b & 7);
+                  const uint64_t x = load_be64(in, sec32 + (b >> 3)) << (b & 7);
                   da = (uint32_t)(x >> (64 - w));
                   if (j + 1 < nd) db = (uint32_t)((x << w) >> (64 - w));
                 }
