@@ -58,12 +58,11 @@ struct Workspace {
   uint32_t* counters = nullptr;  // kBatchCounterWords words
   bool attrs_set = false;
   int sm_count = 0;
-  int smem_per_sm = 0;     // shared memory per SM, bytes
-  int smem_reserved = 0;   // shared memory the system keeps per CTA
   int smem_optin = 0;      // largest dynamic shared memory per CTA
-  // CTAs per SM that threads and registers allow for the CTA-per-chunk RLE
-  // kernels, by family (1, 2, 4) and warps per CTA (1..16); 0 = not known yet
-  mutable int rle_ctas[5][17] = {};
+  // dynamic shared memory per CTA of the CTA-per-chunk RLE kernels at the
+  // CTAs per SM that threads and registers allow, by family (1, 2, 4) and
+  // warps per CTA (1..16); 0 = not known yet, -1 = unknown
+  mutable int rle_avail[5][17] = {};
 };
 
 std::mutex g_mu;
@@ -93,8 +92,6 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
                  {(const void*)batch_kernel, kBatchSmem}};
     e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (auto& at : attrs) {
@@ -196,16 +193,24 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
 int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts) {
   int stage = kRleStageBytes;
   if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;
-  int& ctas = w.rle_ctas[fam][parts];
-  if (ctas == 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 32 * parts, 0) != cudaSuccess) {
-    cudaGetLastError();
-    ctas = -1;
+  // cached per family and warps: the dynamic shared memory a CTA may have
+  // while as many CTAs fit per SM as threads and registers allow (the
+  // runtime accounts for its allocation granularity and reserved memory)
+  int& avail = w.rle_avail[fam][parts];
+  if (avail == 0) {
+    int ctas = 0;
+    size_t bytes = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 32 * parts, 0) != cudaSuccess || ctas <= 0 ||
+        cudaOccupancyAvailableDynamicSMemPerBlock(&bytes, fn, ctas, 32 * parts) != cudaSuccess) {
+      cudaGetLastError();
+      avail = -1;
+    } else {
+      avail = (int)(bytes < (size_t)w.smem_optin ? bytes : (size_t)w.smem_optin);
+    }
   }
-  if (ctas <= 0 || w.smem_per_sm <= 0) return stage;
+  if (avail <= 0) return stage;
   const int other = parts * kRleScratch + kRleCtaExtra;
-  int budget = w.smem_per_sm / ctas - w.smem_reserved;
-  if (budget > w.smem_optin) budget = w.smem_optin;
-  budget -= other;
+  const int budget = avail - other;
   // RLE v1 adds a terminator bitmap of about a quarter of the stage (+384 B)
   int wide = fam == 1 ? (budget - 384) / 5 * 4 : budget;
   wide &= ~255;
