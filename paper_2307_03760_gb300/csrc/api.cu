@@ -58,6 +58,8 @@ struct Workspace {
   uint32_t* counters = nullptr;  // kBatchCounterWords words
   bool attrs_set = false;
   int sm_count = 0;
+  int smem_per_sm = 0;     // shared memory per SM, bytes
+  int smem_reserved = 0;   // shared memory the system keeps per CTA
   int smem_optin = 0;      // largest dynamic shared memory per CTA
   // dynamic shared memory per CTA of the CTA-per-chunk RLE kernels at the
   // CTAs per SM that threads and registers allow, by family (1, 2, 4) and
@@ -92,6 +94,8 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
                  {(const void*)batch_kernel, kBatchSmem}};
     e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (auto& at : attrs) {
@@ -194,18 +198,21 @@ int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts) {
   int stage = kRleStageBytes;
   if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;
   // cached per family and warps: the dynamic shared memory a CTA may have
-  // while as many CTAs fit per SM as threads and registers allow (the
-  // runtime accounts for its allocation granularity and reserved memory)
+  // while as many CTAs fit per SM as threads and registers allow.  A CTA's
+  // share is its dynamic shared memory plus the memory the system reserves
+  // for it, allocated in 128-byte units (measured on GB300 with ncu: one
+  // byte over takes a CTA per SM away).
   int& avail = w.rle_avail[fam][parts];
   if (avail == 0) {
     int ctas = 0;
-    size_t bytes = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 32 * parts, 0) != cudaSuccess || ctas <= 0 ||
-        cudaOccupancyAvailableDynamicSMemPerBlock(&bytes, fn, ctas, 32 * parts) != cudaSuccess) {
+        w.smem_per_sm <= 0) {
       cudaGetLastError();
       avail = -1;
     } else {
-      avail = (int)(bytes < (size_t)w.smem_optin ? bytes : (size_t)w.smem_optin);
+      const int share = (w.smem_per_sm / ctas) & ~127;
+      avail = share - w.smem_reserved;
+      if (avail > w.smem_optin) avail = w.smem_optin;
     }
   }
   if (avail <= 0) return stage;
