@@ -3,7 +3,7 @@ CTA-per-chunk kernels then walk them through a ring and decode one part per
 warp), next to chunks that are staged: bit-exact against the oracle for
 ORC RLE v1, RLE v2 and byte RLE, with every launch shape of the parity
 suite, plus corrupted large chunks whose status must be the first error in
-stream order."""
+stream order, and chunks around the size where the widened stage ends."""
 import numpy as np
 import pytest
 
@@ -24,21 +24,21 @@ from devutil import assert_parity, pack, run_plain  # noqa: E402
 BIG = 240 * 1024
 
 
-def big_rle_v1(rng) -> bytes:
+def big_rle_v1(rng, size=BIG) -> bytes:
     """Literal groups of full-range values: about 9.3 bytes per value."""
     out = bytearray()
-    while len(out) < BIG:
+    while len(out) < size:
         vals = rng.integers(-(1 << 62), 1 << 62, size=128, dtype=np.int64)
         out += v1_literal([int(v) for v in vals], True)
     return bytes(out)
 
 
-def big_rle_v2(rng) -> bytes:
+def big_rle_v2(rng, size=BIG) -> bytes:
     """DIRECT runs of 512 values at width 64 (8 bytes per value), with a
     narrower run now and then so that widths change along the chunk."""
     out = bytearray()
     k = 0
-    while len(out) < BIG:
+    while len(out) < size:
         w = 64 if k % 4 else 56
         vals = rng.integers(0, 1 << 62, size=512, dtype=np.uint64) & np.uint64((1 << w) - 1)
         out += v2_direct([int(v) for v in vals], w)
@@ -46,10 +46,10 @@ def big_rle_v2(rng) -> bytes:
     return bytes(out)
 
 
-def big_byte_rle(rng) -> bytes:
+def big_byte_rle(rng, size=BIG) -> bytes:
     """Literal groups of 128 random bytes (129 stream bytes each)."""
     out = bytearray()
-    while len(out) < BIG:
+    while len(out) < size:
         out.append(0x80)  # -128: 128 literal bytes
         out += rng.integers(0, 256, size=128, dtype=np.uint8).tobytes()
     return bytes(out)
@@ -102,4 +102,20 @@ def test_large_chunks_beside_staged_ones(fmt, parts):
 def test_corrupted_large_chunks(fmt, parts):
     comp, coff, ooff, sst = column(fmt, 9 + fmt, corrupt=True)
     got, st = run_plain(fmt, comp, coff, ooff)
+    assert_parity(fmt, comp, coff, ooff, got, st)
+
+
+@pytest.mark.parametrize("fmt", sorted(MAKE))
+def test_chunks_around_the_stage_limit(fmt, parts):
+    """Compressed sizes from 30 to 50 KiB: staged whole or streamed through
+    rings, depending on the stage each launch shape gets."""
+    rng = np.random.default_rng(77 + fmt)
+    chunks = [MAKE[fmt](rng, size) for size in range(30 * 1024, 50 * 1024, 1536)]
+    comp, coff = pack(chunks)
+    sz, sst = oracle.sizes(fmt, comp, coff)
+    assert (sst == 0).all()
+    ooff = np.zeros(len(chunks) + 1, np.uint64)
+    ooff[1:] = np.cumsum(sz.astype(np.uint64))
+    got, st = run_plain(fmt, comp, coff, ooff)
+    assert (st == 0).all()
     assert_parity(fmt, comp, coff, ooff, got, st)
