@@ -7,7 +7,7 @@
  * each chunk's compressed and uncompressed offsets, so every chunk decodes on
  * its own.  One call decodes many chunks of one format (or, in the batch
  * call, of mixed formats) on one GPU.  The formats are the three the paper
- * evaluates (Sec. VI-A): ORC integer RLE version 1 and version 2 and Deflate
+ * evaluates (Sec. V-A): ORC integer RLE version 1 and version 2 and Deflate
  * (RFC 1951, raw: no zlib or gzip wrapper, no preset dictionary).
  *
  * Memory layout shared by every call (all pointers are DEVICE pointers
@@ -52,7 +52,7 @@ extern "C" {
 
 typedef struct CUstream_st *cudaStream_t;
 
-/* Chunk formats (CODAG Sec. VI-A).  _I64 columns are signed (ORC zigzag
+/* Chunk formats (CODAG Sec. V-A).  _I64 columns are signed (ORC zigzag
  * encoding of bases, literals and deltas as the ORC format defines), _U64
  * unsigned. */
 typedef enum {
@@ -64,7 +64,7 @@ typedef enum {
   /* ORC byte RLE (byte columns; output bytes) and boolean RLE (byte RLE over
    * bytes of eight booleans, most significant bit first; output one 0/1 byte
    * per boolean, output span = number of booleans, the stream must decode to
-   * exactly ceil(span / 8) bytes).  Not evaluated in the paper; Sec. VI-A
+   * exactly ceil(span / 8) bytes).  Not evaluated in the paper; Sec. V-A
    * notes that other encodings can be enabled the same way. */
   CODAG_ORC_BYTE_RLE = 6,
   CODAG_ORC_BOOL_RLE = 7,
@@ -104,8 +104,8 @@ enum {
 /*
  * codag_decompress - decode n_chunks chunks of one format.
  *
- * CODAG Sec. V-C/V-D (warp-level decompression, all lanes decoding) and
- * Sec. V-E/V-F (coalesced on-demand reading and writing): a Deflate chunk is
+ * CODAG Sec. IV-C/IV-D (warp-level decompression, all lanes decoding) and
+ * Sec. IV-E/IV-F (coalesced on-demand reading and writing): a Deflate chunk is
  * decoded by one warp; an RLE chunk by one CTA whose warps decode segments of
  * it after one warp has walked the run headers.  Compressed bytes are staged
  * in shared memory with 1-D TMA bulk copies; output is written with
@@ -292,7 +292,7 @@ codag_status codag_set_parts_per_chunk(int parts);
 int codag_get_parts_per_chunk(void);
 
 /*
- * Input staging of the one-warp-per-chunk decode kernels (CODAG Sec. V-E and
+ * Input staging of the one-warp-per-chunk decode kernels (CODAG Sec. IV-E and
  * its register input buffer): mode 0 stages compressed bytes in a per-warp
  * shared-memory ring filled by TMA bulk copies (default); mode 1 keeps a
  * 512-byte window in the warp's registers, refilled by coalesced loads, and

@@ -1,7 +1,7 @@
 /*
  * Oracle: ORC byte RLE and boolean RLE decoders.  TEST INFRASTRUCTURE ONLY.
  *
- * CODAG Sec. VI-A notes that encodings beyond the evaluated three can be
+ * CODAG Sec. V-A notes that encodings beyond the evaluated three can be
  * enabled through the same decoding structure; ORC's byte run-length
  * encoding (used for byte columns and, over packed bits, for boolean columns
  * and present streams) is such an encoding.  The byte format followed here

@@ -2,7 +2,7 @@
  * Oracle: raw Deflate (RFC 1951) decoder.  TEST INFRASTRUCTURE ONLY.
  *
  * CODAG Sec. II-A: Deflate is dictionary (LZ77) coding whose literals and
- * length/offset pairs are Huffman coded; Sec. V-F gives the back-reference
+ * length/offset pairs are Huffman coded; Sec. IV-F gives the back-reference
  * copy (including the case where the length exceeds the offset and the
  * window repeats, which this decoder defines by copying one byte at a time).
  * The stream format is RFC 1951 Sec. 3.2, followed in its own order:

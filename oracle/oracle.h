@@ -7,7 +7,7 @@
  * the benchmark do.  It shares no code, header, table or helper with the CUDA
  * path: every constant below is written out here again on purpose.
  *
- * What is decoded (CODAG, Sec. II-A and Sec. VI-A): each chunk is an
+ * What is decoded (CODAG, Sec. II-A and Sec. V-A): each chunk is an
  * independently compressed byte stream that decodes on its own; a chunk's
  * output must fill its output span exactly.
  *

@@ -2,7 +2,7 @@
  * Oracle: ORC integer RLE version 1 decoder.  TEST INFRASTRUCTURE ONLY.
  *
  * CODAG Sec. II-A describes RLE v1 as encoding each run by a value and a run
- * length; Sec. VI-A evaluates the Apache ORC form of it.  The byte format
+ * length; Sec. V-A evaluates the Apache ORC form of it.  The byte format
  * followed here is the ORC v1 integer RLE (version 1):
  *
  *   control byte h, read as a signed 8-bit number

@@ -2,7 +2,7 @@
  * Oracle: ORC integer RLE version 2 decoder.  TEST INFRASTRUCTURE ONLY.
  *
  * CODAG Sec. II-A: RLE v2 combines run-length and delta encoding (plus bit
- * packing) over RLE v1; Sec. VI-A evaluates the Apache ORC form.  The format
+ * packing) over RLE v1; Sec. V-A evaluates the Apache ORC form.  The format
  * followed is ORC v1 integer RLE version 2.  The top two bits of a run's
  * first byte select the sub-encoding:
  *

@@ -62,9 +62,10 @@ struct Workspace {
   int smem_reserved = 0;   // shared memory the system keeps per CTA
   int smem_optin = 0;      // largest dynamic shared memory per CTA
   // dynamic shared memory per CTA of the CTA-per-chunk RLE kernels at the
-  // CTAs per SM that threads and registers allow, by family (1, 2, 4) and
-  // warps per CTA (1..16); 0 = not known yet, -1 = unknown
-  mutable int rle_avail[5][17] = {};
+  // CTAs per SM that threads and registers allow, by kernel (decode or
+  // sizes: their register counts differ), family (1, 2, 4) and warps per CTA
+  // (1..16); 0 = not known yet, -1 = unknown
+  mutable int rle_avail[2][5][17] = {};
 };
 
 std::mutex g_mu;
@@ -194,15 +195,15 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
 // fallback path), widened to all the shared memory that the CTAs per SM
 // allowed by threads and registers leave free, so that more chunks are
 // staged whole without costing occupancy.
-int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts) {
+int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts, bool store) {
   int stage = kRleStageBytes;
   if (stage < parts * RleRing::SMEM) stage = parts * RleRing::SMEM;
-  // cached per family and warps: the dynamic shared memory a CTA may have
+  // cached per kernel, family and warps: the dynamic shared memory a CTA may have
   // while as many CTAs fit per SM as threads and registers allow.  A CTA's
   // share is its dynamic shared memory plus the memory the system reserves
   // for it, allocated in 128-byte units (measured on GB300 with ncu: one
   // byte over takes a CTA per SM away).
-  int& avail = w.rle_avail[fam][parts];
+  int& avail = w.rle_avail[store ? 1 : 0][fam][parts];
   if (avail == 0) {
     int ctas = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 32 * parts, 0) != cudaSuccess || ctas <= 0 ||
@@ -273,7 +274,7 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     if (fam == 1) fn = store ? (const void*)rle_v1_kernel : (const void*)rle_v1_sizes_kernel;
     else if (fam == 4) fn = (const void*)byte_rle_cta_kernel;
     else fn = store ? (const void*)rle_v2_kernel : (const void*)rle_v2_sizes_kernel;
-    const int stage = rle_stage_bytes(*w, fn, fam, parts);
+    const int stage = rle_stage_bytes(*w, fn, fam, parts, store);
     a.stage_bytes = stage;
     smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
     if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);

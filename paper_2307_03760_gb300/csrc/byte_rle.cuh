@@ -1,4 +1,4 @@
-// ORC byte RLE and boolean RLE, one warp per chunk.  CODAG Sec. VI-A: other
+// ORC byte RLE and boolean RLE, one warp per chunk.  CODAG Sec. V-A: other
 // encodings are enabled through the same structure (a chunk per decoding
 // unit, the staged input stream, warp-wide writes); ORC's byte run-length
 // encoding is one.  Stream format: control byte h (int8); h >= 0: the next

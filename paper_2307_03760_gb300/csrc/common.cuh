@@ -1,8 +1,8 @@
 // Shared device primitives for the chunk decoders (sm_103a).
 //
 // A "decoder" is one warp that owns one compressed chunk at a time (CODAG
-// Sec. V-C: the decompression unit is a warp, every lane follows the same
-// control flow and holds the same decoding state, Sec. V-D).  This file holds
+// Sec. IV-C: the decompression unit is a warp, every lane follows the same
+// control flow and holds the same decoding state, Sec. IV-D).  This file holds
 // what all formats share: per-chunk status codes, PTX wrappers for the 1-D
 // TMA bulk copy and mbarriers used by the input staging ring, and small
 // bit/byte helpers.

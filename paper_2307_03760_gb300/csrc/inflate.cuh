@@ -1,5 +1,5 @@
 // Raw Deflate (RFC 1951) decoder, one warp per chunk (CODAG Sec. II-A,
-// Deflate; Sec. V-F for the dictionary copy primitive).
+// Deflate; Sec. IV-F for the dictionary copy primitive).
 //
 // Work split inside the warp:
 //   - the bit stream is consumed by every lane from a 64-bit register buffer
@@ -11,13 +11,16 @@
 //   - tables are built warp-parallel for every block: __match_any_sync ranks
 //     symbols of equal length (canonical order), and each lane fills table
 //     entries by locating the code that prefixes the entry's bits;
-//   - output goes into a shared-memory window that mirrors the last WIN
-//     bytes of the chunk's output; literals are stored by one lane, matches
-//     (the paper's memcpy(off, len), Table 2) are copied by all lanes, lane i
+//   - output and match sources live in global memory (the chunk's own output
+//     span, served by L1/L2): literals are stored by one lane; a match (the
+//     paper's memcpy(off, len), Table 2) is copied by all lanes, lane i
 //     taking byte i, with overlapping matches (len > dist) handled by reading
-//     position (i mod dist) of the source window (Sec. V-F); sources farther
-//     back than the window are read back from global memory;
-//   - the window is flushed to global memory with coalesced 16-byte stores.
+//     position (i mod dist) of the source (Sec. IV-F); in the lean loop a
+//     short match's source bytes are loaded when it is decoded and stored
+//     when the next match is decoded, so the load overlaps decoding;
+//   - a shared-memory window of the last WIN output bytes is a template
+//     option (WIN > 0: flushed with 16-byte stores); every kernel compiles it
+//     with WIN = 0, since the window cost more occupancy than it saved.
 //
 // Status order matches the oracle: the first problem met in stream order;
 // code-length problems before symbol validity (a code whose bits run past the

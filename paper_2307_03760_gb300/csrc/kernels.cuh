@@ -1,6 +1,6 @@
 // Kernel entry points and their per-warp shared-memory layouts.
 //
-// Work mapping (CODAG Sec. II-B and V-C): every chunk is independent; one
+// Work mapping (CODAG Sec. II-B and IV-C): every chunk is independent; one
 // warp decodes one chunk.  The plain kernels launch one warp per chunk and
 // let the block scheduler hand out chunks; the batch kernel is persistent
 // (one wave of CTAs) and its warps claim chunks with an atomic counter in

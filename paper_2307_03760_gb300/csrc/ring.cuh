@@ -1,4 +1,4 @@
-// Per-decoder input staging ring (CODAG Sec. V-E, "coalesced on-demand
+// Per-decoder input staging ring (CODAG Sec. IV-E, "coalesced on-demand
 // reading": a warp refills an input buffer with whole cache lines when it has
 // room, and decoding then reads from the buffer).
 //
@@ -177,7 +177,7 @@ struct InRing {
   }
 };
 
-// Register staging ring (CODAG Sec. V-E, the register input buffer): the
+// Register staging ring (CODAG Sec. IV-E, the register input buffer): the
 // warp keeps a 512-byte window of the chunk in registers, 8 bytes per lane in
 // each of two 256-byte halves, plus the next 256 bytes already requested;
 // ensure() slides the window forward by halves.  A read takes its bytes from

@@ -1,10 +1,13 @@
-// ORC integer RLE v1 decoder, one warp per chunk (CODAG Sec. II-A, RLE v1;
-// Sec. VI-A evaluates the ORC form).  Stream format: control byte h (int8);
-// h >= 0: run of h+3 values = base + i*delta (int8 delta byte, base varint);
-// h < 0: -h literal varints.  Signed columns zigzag base and literals.
+// ORC integer RLE v1 decoder (CODAG Sec. II-A, RLE v1; Sec. V-A evaluates
+// the ORC form).  Stream format: control byte h (int8); h >= 0: run of h+3
+// values = base + i*delta (int8 delta byte, base varint); h < 0: -h literal
+// varints.  Signed columns zigzag base and literals.
+//
+// As for RLE v2, the plain kernels give a chunk one CTA whose warps decode
+// group-aligned segments; the functions here decode one part with one warp.
 //
 // Work split inside the warp:
-//   - group headers are read by every lane (identical state, Sec. V-D);
+//   - group headers are read by every lane (identical state, Sec. IV-D);
 //   - a varint is decoded from one 8-byte window with shifts and masks
 //     instead of a byte-at-a-time loop;
 //   - a literal group's varint boundaries are found warp-parallel: each lane

@@ -1,6 +1,11 @@
-// ORC integer RLE v2 decoder, one warp per chunk (CODAG Sec. II-A, RLE v2;
-// Sec. VI-A evaluates the ORC form).  The top two bits of a run's first byte
-// select SHORT_REPEAT / DIRECT / PATCHED_BASE / DELTA.
+// ORC integer RLE v2 decoder (CODAG Sec. II-A, RLE v2; Sec. V-A evaluates
+// the ORC form).  The top two bits of a run's first byte select
+// SHORT_REPEAT / DIRECT / PATCHED_BASE / DELTA.
+//
+// A chunk is decoded by one CTA in the plain kernels (a walk over the run
+// headers cuts it into segments at run boundaries, and each warp decodes the
+// segments it claims) and by one or more warps in the batch kernel.  The
+// functions here decode one part (a run-aligned sub-stream) with one warp.
 //
 // Work split inside the warp:
 //   - run headers are parsed by every lane (identical state);

@@ -11,7 +11,7 @@
  * chunk) pair gives the same bytes on any host.
  *
  * Column shapes (stand-ins for the paper's datasets, which are not public in
- * this form; CODAG Sec. VI-B, Tables 4 and 5):
+ * this form; CODAG Sec. V-B, Tables 4 and 5):
  *   RLE v1: groups chosen by count, 70% runs (length U[3,130], delta
  *           U[-128,127], base ~ N(0, 2^20)) and 30% literal groups (count
  *           U[1,128], values log-uniform in [1, 2^40] with a random sign);
