@@ -9,6 +9,7 @@
 
 #include "../../include/codag.h"
 #include "kernels.cuh"
+#include "inflate_lanes.cuh"  // after kernels.cuh: uses Args
 
 using namespace codag;
 
@@ -37,6 +38,12 @@ constexpr int kMaxDevices = 64;
 constexpr uint64_t kSliceBytes = 16ull << 20;
 constexpr int kMaxSlices = 64;
 constexpr int kPipeDecode = 4;
+
+// Two-pass Deflate command pool: words per chunk at first (a 64 KiB chunk
+// of any content fits), the most per chunk, and the most in all.
+constexpr uint32_t kHufCapInit = 16384;
+constexpr uint32_t kHufCapMax = 1u << 22;
+constexpr uint64_t kHufPoolMaxWords = 1ull << 30;
 struct HostPipe {
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaStream_t dec[kPipeDecode] = {};
@@ -66,6 +73,19 @@ struct Workspace {
   // sizes: their register counts differ), family (1, 2, 4) and warps per CTA
   // (1..16); 0 = not known yet, -1 = unknown
   mutable int rle_avail[2][5][17] = {};
+  // two-pass Deflate: the copy-command pool (hcap words per chunk), the
+  // per-chunk command counts, chunk-claim counters (one per concurrent slice
+  // of codag_decompress_host, one for plain calls), and the largest command
+  // count the decoder has seen (a device word, copied to pinned host memory
+  // after each call; the next call sizes its pool from it)
+  uint32_t* hcmd = nullptr;
+  uint64_t hcmd_words = 0;
+  uint32_t hcap = kHufCapInit;
+  uint32_t* hncmd = nullptr;
+  uint64_t hncmd_cap = 0;
+  uint32_t* hctr = nullptr;
+  unsigned long long* hneed = nullptr;
+  unsigned long long* hneed_host = nullptr;
 };
 
 std::mutex g_mu;
@@ -93,7 +113,9 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)byte_rle_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
-                 {(const void*)batch_kernel, kBatchSmem}};
+                 {(const void*)batch_kernel, kBatchSmem},
+                 {(const void*)inflate_huffman_kernel, kHufSmem},
+                 {(const void*)inflate_huffman_sizes_kernel, kHufSmem}};
     e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&w.smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
@@ -161,10 +183,82 @@ codag_status check_common(const void* comp, const uint64_t* comp_offsets, uint64
   return CODAG_OK;
 }
 
+// One launch's share of the two-pass Deflate scratch.
+struct DeflateRun {
+  uint32_t* cmd = nullptr;  // the launch's first chunk's command slot
+  uint32_t cap = 0;         // command words per chunk
+  uint32_t* ncmd = nullptr; // the launch's first chunk's count
+  uint32_t* counter = nullptr;
+  unsigned long long* need = nullptr;
+};
+
+// Size the two-pass Deflate scratch for a call of n chunks (store: with the
+// command pool).  The per-chunk capacity grows to what an earlier call
+// needed (plus an eighth); a chunk that still does not fit is decoded by the
+// one-warp decoder instead, so the capacity is a speed setting only.
+codag_status deflate_prepare(Workspace& w, uint64_t n, bool store, uint32_t* cap_out) {
+  if (!w.hctr) {
+    if (cudaMalloc(&w.hctr, (kMaxSlices + 1) * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&w.hneed, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(w.hneed, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaHostAlloc(&w.hneed_host, sizeof(unsigned long long), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CODAG_ENOMEM, "Deflate workspace allocation failed");
+    }
+    *w.hneed_host = 0;
+  }
+  *cap_out = 0;
+  if (!store) return CODAG_OK;
+  const unsigned long long need = *reinterpret_cast<volatile unsigned long long*>(w.hneed_host);
+  if (need > w.hcap) {
+    const unsigned long long want = (need + need / 8 + 255) & ~255ull;
+    w.hcap = want > kHufCapMax ? kHufCapMax : (uint32_t)want;
+  }
+  uint64_t cap = w.hcap;
+  if (n * cap > kHufPoolMaxWords) cap = kHufPoolMaxWords / n;
+  const uint64_t words = n * cap;
+  if (words > w.hcmd_words) {
+    if (w.hcmd) cudaFree(w.hcmd);
+    w.hcmd = nullptr;
+    w.hcmd_words = 0;
+    const uint64_t alloc = words + words / 4;
+    if (cudaMalloc(&w.hcmd, alloc * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CODAG_ENOMEM, "Deflate command pool allocation failed");
+    }
+    w.hcmd_words = alloc;
+  }
+  if (n > w.hncmd_cap) {
+    if (w.hncmd) cudaFree(w.hncmd);
+    w.hncmd = nullptr;
+    w.hncmd_cap = 0;
+    const uint64_t alloc = n < 1024 ? 1024 : n + n / 4;
+    if (cudaMalloc(&w.hncmd, alloc * sizeof(uint32_t)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CODAG_ENOMEM, "Deflate count allocation failed");
+    }
+    w.hncmd_cap = alloc;
+  }
+  *cap_out = (uint32_t)cap;
+  return CODAG_OK;
+}
+
+// The scratch of chunks [first, first + n) of a prepared call, claimed
+// through counter `slot` (0 .. kMaxSlices).
+DeflateRun deflate_run(const Workspace& w, uint32_t cap, uint64_t first, int slot) {
+  DeflateRun r;
+  r.cap = cap;
+  r.cmd = w.hcmd ? w.hcmd + first * cap : nullptr;
+  r.ncmd = w.hncmd ? w.hncmd + first : nullptr;
+  r.counter = w.hctr + slot;
+  r.need = w.hneed;
+  return r;
+}
+
 codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
                            const uint64_t* comp_offsets, uint64_t n, void* out,
                            const uint64_t* out_offsets, uint64_t* sizes, bool store,
-                           int32_t* status, cudaStream_t stream);
+                           int32_t* status, cudaStream_t stream, const DeflateRun* dr = nullptr);
 
 codag_status launch_plain(int format, const void* comp, const uint64_t* comp_offsets, uint64_t n,
                           void* out, const uint64_t* out_offsets, uint64_t* sizes, bool store,
@@ -186,6 +280,19 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   if ((s = current_ws(&w)) != CODAG_OK) return s;
   if ((s = grow_status(*w, n)) != CODAG_OK) return s;
   w->last_n = n;
+  if (fam == 3) {
+    uint32_t cap;
+    if ((s = deflate_prepare(*w, n, store, &cap)) != CODAG_OK) return s;
+    const DeflateRun dr = deflate_run(*w, cap, 0, kMaxSlices);
+    s = launch_kernel(*w, format, comp, comp_offsets, n, out, out_offsets, sizes, store, w->status,
+                      stream, &dr);
+    if (s == CODAG_OK && store) {
+      const cudaError_t e = cudaMemcpyAsync(w->hneed_host, w->hneed, sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "Deflate need copy");
+    }
+    return s;
+  }
   return launch_kernel(*w, format, comp, comp_offsets, n, out, out_offsets, sizes, store, w->status,
                        stream);
 }
@@ -231,7 +338,7 @@ int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts, bool
 codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
                            const uint64_t* comp_offsets, uint64_t n, void* out,
                            const uint64_t* out_offsets, uint64_t* sizes, bool store,
-                           int32_t* status, cudaStream_t stream) {
+                           int32_t* status, cudaStream_t stream, const DeflateRun* dr) {
   const Workspace* w = &ws;
   const int fam = family_of(format);
   Args a{};
@@ -250,6 +357,33 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   // in registers instead of a shared-memory ring (codag_set_input_staging);
   // byte / boolean RLE then runs a warp per chunk, else a CTA per chunk
   const bool reg = store && (fam == 3 || fam == 4) && g_reg_ring[fam].load() == 1;
+  if (fam == 3 && !reg && dr) {
+    // two passes: Huffman decoding a lane per chunk, then the copies a warp
+    // per chunk, then the one-warp decoder for chunks left to it
+    HufArgs h{dr->cmd, dr->cap, dr->ncmd, dr->counter, dr->need};
+    cudaError_t e = cudaMemsetAsync(dr->counter, 0, sizeof(uint32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    const uint64_t lanes = 32ull * kHufWarps;
+    const unsigned g1 = (unsigned)((n + lanes - 1) / lanes < (uint64_t)w->sm_count ? (n + lanes - 1) / lanes
+                                                                                   : (uint64_t)w->sm_count);
+    if (!store) {
+      inflate_huffman_sizes_kernel<<<g1, 32 * kHufWarps, kHufSmem, stream>>>(a, h);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+      g_launches.fetch_add(1);
+      return CODAG_OK;
+    }
+    inflate_huffman_kernel<<<g1, 32 * kHufWarps, kHufSmem, stream>>>(a, h);
+    inflate_lz77_kernel<<<(unsigned)((n + kLz77Warps - 1) / kLz77Warps), 32 * kLz77Warps, 0, stream>>>(a, h);
+    Args b = a;
+    b.deferred_only = 1;
+    inflate_kernel<<<(unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock), kThreads,
+                     kWarpsPerBlock * kDeflateWarp, stream>>>(b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    g_launches.fetch_add(3);
+    return CODAG_OK;
+  }
   if (fam == 3 || fam == 5 || (fam == 4 && (!store || reg))) {
     grid = (unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock);
     block = kThreads;
@@ -444,6 +578,8 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
   HostPipe& p = w->pipe;
   if ((s = init_pipe(p)) != CODAG_OK) return s;
   if ((s = grow_offs(p, 2 * (n + 1))) != CODAG_OK) return s;
+  uint32_t hcap = 0;
+  if (family_of(format) == 3 && (s = deflate_prepare(*w, n, true, &hcap)) != CODAG_OK) return s;
   w->last_n = n;
   // a Deflate or byte RLE decoder is one warp (about 40 resident per SM), an RLE decoder
   // a CTA (a few per SM)
@@ -482,8 +618,9 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
     if (e == cudaSuccess) e = cudaEventRecord(p.copied[k], p.h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, p.copied[k], 0);
     if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy in");
+    const DeflateRun dr = deflate_run(*w, hcap, a, (int)k);
     s = launch_kernel(*w, format, d_comp, d_coff + a, b - a, d_out, d_ooff + a, nullptr, true,
-                      w->status + a, ds);
+                      w->status + a, ds, family_of(format) == 3 ? &dr : nullptr);
     if (s != CODAG_OK) return s;
     e = cudaEventRecord(p.decoded[k], ds);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p.d2h, p.decoded[k], 0);
@@ -493,6 +630,8 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
     if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy out");
   }
   if (h_status) e = cudaMemcpyAsync(h_status, w->status, n * 4, cudaMemcpyDeviceToHost, p.d2h);
+  if (e == cudaSuccess && family_of(format) == 3)
+    e = cudaMemcpyAsync(w->hneed_host, w->hneed, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p.d2h);
   if (e == cudaSuccess) e = cudaEventRecord(p.done, p.d2h);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, p.done, 0);
   if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host finish");

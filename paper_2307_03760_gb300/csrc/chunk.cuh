@@ -327,6 +327,7 @@ __device__ __forceinline__ void warp_chunk_body(const Args& a) {
   const uint32_t warp = threadIdx.x >> 5;
   const uint64_t c = (uint64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (c >= a.n) return;
+  if (a.deferred_only && a.status[c] != kDeferred) return;
   uint8_t* region = smem + warp * kWarpSmem;
   Ring ring;
   ring.init(region);

@@ -26,6 +26,9 @@ enum ChunkStatus : int32_t {
   ST_BAD_SPAN = 8,
   ST_TIMEOUT = 9,
 };
+// Internal status (never returned): a Deflate chunk the two-pass decoder
+// left to the one-warp decoder, which then writes its final status.
+constexpr int32_t kDeferred = 0x40;
 
 // Format identifiers (C ABI values).
 enum Format : int {

@@ -79,6 +79,7 @@ struct Args {
   uint32_t* counter;       // batch kernel: kBatchCounterWords words, zeroed before launch
   unsigned long long* keys;  // batch kernel: combined status of multi-part chunks
   int stage_bytes;           // plain RLE kernels: shared staging area per CTA
+  int deferred_only;         // one-warp Deflate kernel: decode only chunks whose status is kDeferred
 };
 
 // Batch scratch: [0] task counter, [1..128] bucket histogram, [129..256]
@@ -123,6 +124,15 @@ __global__ void rle_v2_kernel(Args a);
 __global__ void rle_v2_sizes_kernel(Args a);
 __global__ void inflate_kernel(Args a);
 __global__ void inflate_sizes_kernel(Args a);
+
+// Two-pass raw Deflate (inflate_lanes.cuh): Huffman decoding with one lane
+// per chunk (persistent CTAs of kHufWarps warps, chunks claimed through
+// h.counter), then the LZ77 copies with one warp per chunk.  The sizes
+// kernel runs the first pass alone, without output or commands.
+struct HufArgs;
+__global__ void inflate_huffman_kernel(Args a, HufArgs h);
+__global__ void inflate_huffman_sizes_kernel(Args a, HufArgs h);
+__global__ void inflate_lz77_kernel(Args a, HufArgs h);
 
 // Persistent batch kernel: warps claim (chunk, part) tasks in bucket order.
 __global__ void batch_kernel(Args a);
