@@ -79,7 +79,7 @@ __device__ __forceinline__ uint32_t lane_sym_entry(int kind, uint32_t len, uint3
 struct LaneTables {
   uint16_t lit[(1 << kLaneLTB) * 32];  // also the lane's code lengths while a header is read
   uint16_t dist[(1 << kLaneDTB) * 32];  // also the code-length code's table
-  uint16_t lsort[288 * 32];  // symbol | length << 12, in canonical order
+  uint16_t lsort[288 * 32];  // table entries of the symbols, in canonical order
   uint16_t dsort[32 * 32];
   uint16_t lmeta[2 * (15 - kLaneLTB) * 32];  // limits, then bases, of lengths LTB+1..15
   uint16_t dmeta[2 * (15 - kLaneDTB) * 32];
@@ -156,7 +156,7 @@ __device__ int32_t lane_build(const uint16_t* lens, int n, int kind, uint16_t* t
     if (L) {
       const uint32_t p = pos.get(L);
       pos.add(L, 1);
-      sorted[p * 32] = (uint16_t)(k | (L << 12));
+      sorted[p * 32] = (uint16_t)lane_sym_entry(kind, L, (uint32_t)k);
     }
   }
   // table: entry t in code order (prefix t, most significant code bit
@@ -169,10 +169,8 @@ __device__ int32_t lane_build(const uint16_t* lens, int n, int kind, uint16_t* t
   uint32_t idx = 0, end = 0, ent = dflt;
   for (uint32_t t = 0; t < (1u << TB); t++) {
     if (t == end && idx < nshort) {
-      const uint32_t s = sorted[idx * 32];
-      const uint32_t L = s >> 12;
-      ent = lane_sym_entry(kind, L, s & 0xfffu);
-      end += 1u << (TB - L);
+      ent = sorted[idx * 32];
+      end += 1u << (TB - (ent & 15));
       idx++;
     }
     tab[(__brev(t) >> (32 - TB)) * 32] = (uint16_t)(t < end ? ent : dflt);
@@ -187,12 +185,12 @@ __device__ int32_t lane_build(const uint16_t* lens, int n, int kind, uint16_t* t
   return ST_OK;
 }
 
-// A code longer than TB bits, from the next 15 stream bits.  Only complete
-// codes have such entries, so the search always ends at a code; NS bounds
-// the index into sorted all the same.
+// A code longer than TB bits, from the next 15 stream bits: its table entry
+// (sorted holds the entries of all symbols in canonical order).  Only
+// complete codes have such entries, so the search always ends at a code; NS
+// bounds the index into sorted all the same.
 template <int TB, uint32_t NS>
-__device__ __forceinline__ uint32_t lane_long(uint64_t bb, const uint16_t* meta, const uint16_t* sorted,
-                                              int kind) {
+__device__ __forceinline__ uint32_t lane_long(uint64_t bb, const uint16_t* meta, const uint16_t* sorted) {
   const uint32_t rev = __brev((uint32_t)bb) >> 17;
   uint32_t L = 15;
 #pragma unroll
@@ -200,8 +198,7 @@ __device__ __forceinline__ uint32_t lane_long(uint64_t bb, const uint16_t* meta,
     if (rev < meta[i * 32]) L = TB + 1 + i;
   const uint32_t base = meta[(15 - TB + L - TB - 1) * 32];
   const uint32_t k = (base + (rev >> (15 - L))) & 0xffffu;
-  const uint32_t s = sorted[(k < NS ? k : NS - 1) * 32];
-  return lane_sym_entry(kind, L, s & 0xfffu);
+  return sorted[(k < NS ? k : NS - 1) * 32];
 }
 
 // Per-lane bit reader over global memory.  Reader position r = chunk
@@ -218,13 +215,17 @@ struct LaneIn {
   uint64_t bb;
   uint64_t q0, q1, q2, q3;
 
-  __device__ __forceinline__ uint64_t word(uint32_t k) const {
-    const uint8_t* p = g8 + 8ull * k;
-    if (p + 8 <= end) return __ldg(reinterpret_cast<const unsigned long long*>(p));
+  // the word at reader position 8 k; bytes past the buffer read as zero
+  __device__ static __noinline__ uint64_t word_tail(const uint8_t* p, const uint8_t* end) {
     uint64_t v = 0;
     for (int b = 0; b < 8; b++)
       if (p + b < end) v |= (uint64_t)__ldg(p + b) << (8 * b);
     return v;
+  }
+  __device__ __forceinline__ uint64_t word(uint32_t k) const {
+    const uint8_t* p = g8 + 8ull * k;
+    if (p + 8 <= end) return __ldg(reinterpret_cast<const unsigned long long*>(p));
+    return word_tail(p, end);
   }
   __device__ __forceinline__ void seek(uint32_t chunk_pos) {
     ipos = chunk_pos + skew;
@@ -288,6 +289,8 @@ struct LaneDec {
   uint32_t wpos, cap;
   uint32_t run;   // literals since the last command
   uint32_t ncmd;
+  uint32_t ccap;  // command words of the chunk's slot
+  bool stuck;     // the fast step met a symbol it leaves to step()
   uint8_t* out;
   uint32_t* cmd;
   const uint16_t* lt;  // lit/len table, element stride ls
@@ -296,7 +299,7 @@ struct LaneDec {
   LaneIn in;
 
   __device__ __forceinline__ void emit_cmd(uint32_t v) {
-    if (ncmd < h->cap) cmd[ncmd] = v;
+    if (ncmd < ccap) cmd[ncmd] = v;
     ncmd++;
   }
   __device__ __forceinline__ void emit_literal(uint32_t byte) {
@@ -314,8 +317,8 @@ struct LaneDec {
     if (STORE && st == ST_OK) {
       if (run) emit_cmd(0x80000000u | run);
       run = 0;
-      if (ncmd > h->cap) {
-        atomicMax(h->need, 2ull * h->cap);
+      if (ncmd > ccap) {
+        atomicMax(h->need, 2ull * ccap);
         st = kDeferred;
       } else {
         atomicMax(h->need, (unsigned long long)ncmd);
@@ -339,6 +342,8 @@ struct LaneDec {
     wpos = 0;
     run = 0;
     ncmd = 0;
+    stuck = false;
+    ccap = h->cap;
     cap = 0xffffffffu;
     if (ce < cs || ce > total) {
       finish(ST_BAD_SPAN);
@@ -498,6 +503,59 @@ struct LaneDec {
     state = LS_IN_BLOCK;
   }
 
+  // The common step, far from both ends of the chunk: a literal (two when
+  // the next code is a table literal too) or a length/distance pair.  Both
+  // outcomes are computed and the stores predicated, so the lanes of a warp
+  // (each on its own chunk) follow one instruction stream whatever symbol
+  // each meets; only codes longer than the tables and the rare cases branch.
+  // End of block, invalid codes and distances park the lane (stuck): the
+  // next service phase decodes the same symbol again with step(), which makes
+  // every check; nothing is consumed before that.
+  __device__ __forceinline__ void fast_step() {
+    constexpr uint32_t LM = (1u << kLaneLTB) - 1, DM = (1u << kLaneDTB) - 1;
+    in.refill();
+    const uint64_t bb = in.bb;
+    uint32_t e = lt[(uint32_t)(bb & LM) * ls];
+    if ((e >> 13) == K_LONG) e = lane_long<kLaneLTB, 288>(bb, T->lmeta + lane, T->lsort + lane);
+    const uint32_t k = e >> 13;
+    const bool islit = k == K_LIT;
+    const uint32_t L = e & 15;
+    const uint32_t x = islit ? 0u : (e >> 9) & 7;
+    const uint32_t s1 = L + x;
+    const uint64_t b1 = bb >> s1;
+    const uint16_t* t2 = islit ? lt : dt;
+    uint32_t e2 = t2[((uint32_t)b1 & (islit ? LM : DM)) * (islit ? ls : ds)];
+    if (!islit && (e2 >> 13) == K_LONG) e2 = lane_long<kLaneDTB, 32>(b1, T->dmeta + lane, T->dsort + lane);
+    const uint32_t k2 = e2 >> 13;
+    const uint32_t L2 = e2 & 15;
+    const uint32_t x2 = (e2 >> 9) & 15;
+    const uint32_t mlen = F->len_base[(e >> 4) & 31] + ((uint32_t)(bb >> L) & ((1u << x) - 1));
+    const uint32_t d = F->dist_base[(e2 >> 4) & 31] + ((uint32_t)(b1 >> L2) & ((1u << x2) - 1));
+    if (k > K_BASE || (!islit && (k2 != K_BASE || d > wpos))) {
+      stuck = true;
+      return;
+    }
+    const bool two = islit && k2 == K_LIT && (!STORE || wpos + 1 < cap);
+    in.consume(islit ? (two ? L + L2 : L) : s1 + L2 + x2);
+    const uint32_t n = two ? 2u : 1u;
+    if (STORE) {
+      const bool flush = islit && run + n > 255;
+      if (islit) out[wpos] = (uint8_t)(e >> 4);
+      if (two) out[wpos + 1] = (uint8_t)(e2 >> 4);
+      const bool put = flush || !islit;
+      const uint32_t cv = islit ? (0x80000000u | run) : (run | ((mlen - 3) << 8) | ((d - 1) << 16));
+      if (put && ncmd < ccap) cmd[ncmd] = cv;
+      ncmd += put ? 1u : 0u;
+      run = islit ? (flush ? n : run + n) : 0u;
+    }
+    wpos += islit ? n : mlen;
+  }
+  // whether fast_step() may run: 48 bits (the longest step) are left in the
+  // chunk and 258 + 2 bytes in the output span
+  __device__ __forceinline__ bool fast_ok() const {
+    return in.avail() >= 64 && (!STORE || cap - wpos >= 260);
+  }
+
   // One symbol (state LS_IN_BLOCK), and a second one when both are table
   // literals.  The checks and their order are the serial decoder's.
   __device__ void step() {
@@ -505,7 +563,7 @@ struct LaneDec {
     in.refill();
     uint32_t avail = in.avail();
     uint32_t e = lt[(uint32_t)(in.bb & LM) * ls];
-    if ((e >> 13) == K_LONG) e = lane_long<kLaneLTB, 288>(in.bb, T->lmeta + lane, T->lsort + lane, 1);
+    if ((e >> 13) == K_LONG) e = lane_long<kLaneLTB, 288>(in.bb, T->lmeta + lane, T->lsort + lane);
     const uint32_t L = e & 15;
     const uint32_t k = e >> 13;
     if (L > avail) return finish(ST_TRUNCATED);
@@ -536,7 +594,7 @@ struct LaneDec {
     in.consume(L + x);
     avail -= L + x;
     uint32_t ed = dt[(uint32_t)(in.bb & DM) * ds];
-    if ((ed >> 13) == K_LONG) ed = lane_long<kLaneDTB, 32>(in.bb, T->dmeta + lane, T->dsort + lane, 2);
+    if ((ed >> 13) == K_LONG) ed = lane_long<kLaneDTB, 32>(in.bb, T->dmeta + lane, T->dsort + lane);
     const uint32_t Ld = ed & 15;
     if (Ld > avail) return finish(ST_TRUNCATED);
     if ((ed >> 13) != K_BASE) return finish(ST_BAD_HUFFMAN);
@@ -600,14 +658,28 @@ __device__ void huffman_body(const Args& a, const HufArgs& h) {
       if (s.state == LS_NEED_HEADER) s.header();
       while (s.state == LS_NEED_CHUNK) s.claim();
     }
+    // hot loop: only the fast step; it ends when no lane can take one, or
+    // every 8 steps when a quarter of the live lanes wait (header, new
+    // chunk, or a symbol the fast step leaves to the exact one)
     for (uint32_t it = 0;; it++) {
-      const uint32_t am = __ballot_sync(FULL, s.state == LS_IN_BLOCK);
+      const bool act = s.state == LS_IN_BLOCK && !s.stuck && s.fast_ok();
+      const uint32_t am = __ballot_sync(FULL, act);
       if (!am) break;
       if ((it & 7) == 7) {
-        const uint32_t wm = __ballot_sync(FULL, s.state == LS_NEED_HEADER || s.state == LS_NEED_CHUNK);
-        if (4 * __popc(wm) >= __popc(wm | am)) break;
+        const uint32_t live = __ballot_sync(FULL, s.state != LS_GONE);
+        if (4 * __popc(am) <= 3 * __popc(live)) break;
       }
-      if (s.state == LS_IN_BLOCK) s.step();
+      if (act) s.fast_step();
+    }
+    // service: lanes in a block that cannot take a fast step take exact
+    // steps until they can again (or leave the block), a bounded number
+    for (int j = 0; j < 64; j++) {
+      const bool need = s.state == LS_IN_BLOCK && (s.stuck || !s.fast_ok());
+      if (!__any_sync(FULL, need)) break;
+      if (need) {
+        s.stuck = false;
+        s.step();
+      }
     }
   }
 }
