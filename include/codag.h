@@ -104,12 +104,17 @@ enum {
 /*
  * codag_decompress - decode n_chunks chunks of one format.
  *
- * CODAG Sec. IV-C/IV-D (warp-level decompression, all lanes decoding) and
- * Sec. IV-E/IV-F (coalesced on-demand reading and writing): a Deflate chunk is
- * decoded by one warp; an RLE chunk by one CTA whose warps decode segments of
- * it after one warp has walked the run headers.  Compressed bytes are staged
- * in shared memory with 1-D TMA bulk copies; output is written with
- * coalesced stores.
+ * CODAG Sec. IV-C/IV-D (warp-level decompression) and Sec. IV-E/IV-F
+ * (coalesced on-demand reading and writing): an RLE chunk is decoded by one
+ * CTA whose warps decode segments of it after one warp has walked the run
+ * headers, its compressed bytes staged in shared memory with 1-D TMA bulk
+ * copies.  Raw Deflate runs in two passes: Huffman decoding with one lane
+ * per chunk, which stores literals in place and writes 32-bit copy commands
+ * to a library pool (about a quarter of the decoded size; see
+ * codag_set_deflate_pool_limit), then the LZ77 copies with one warp per
+ * chunk writing 32 consecutive output bytes per step; a chunk whose
+ * commands do not fit its part of the pool is decoded by one warp instead
+ * (the same result).  Output is written with coalesced stores.
  *
  * format        one of codag_format.
  * comp, comp_offsets, out, out_offsets: see the layout above (device).
@@ -298,12 +303,28 @@ int codag_get_parts_per_chunk(void);
  * 512-byte window in the warp's registers, refilled by coalesced loads, and
  * reads it with __shfl_sync (no shared memory for the input).  format: a
  * Deflate or byte / boolean RLE format (the setting is per decoder family;
- * RLE v1/v2 always stage in shared memory).  Process-wide; an autotuner
- * choice.  Returns CODAG_EINVAL for another format or mode; the getter
- * returns -1 for another format.
+ * RLE v1/v2 always stage in shared memory).  For Deflate, mode 0 selects the
+ * two-pass decoder (see codag_decompress) and mode 1 the one-warp decoder
+ * with the register ring.  Process-wide; an autotuner choice.  Returns
+ * CODAG_EINVAL for another format or mode; the getter returns -1 for another
+ * format.
  */
 codag_status codag_set_input_staging(int format, int mode);
 int codag_get_input_staging(int format);
+
+/*
+ * codag_set_deflate_pool_limit - upper bound, in bytes, on the command pool
+ * of the two-pass Deflate decoder (0, the default: no bound).  Chunk c owns
+ * the pool words from (out_offsets[c] - out_offsets[0]) / 4 + 2c on (a
+ * quarter of the decoded size of the call, plus two words a chunk); the
+ * pool starts at 64 MiB and grows to what the previous call needed, and a
+ * chunk whose part lies past it or past this bound is decoded by the
+ * one-warp decoder instead, with the same result.  For callers that
+ * bound the library's device memory, and for tests of that fallback.  The
+ * library's addition; the paper has no counterpart.  Process-wide.
+ */
+codag_status codag_set_deflate_pool_limit(uint64_t bytes);
+uint64_t codag_get_deflate_pool_limit(void);
 
 /* Number of kernel launches the library enqueued since load (all calls). */
 uint64_t codag_kernel_launches(void);

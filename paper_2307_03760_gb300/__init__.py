@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
         L.codag_set_input_staging.restype = i32
         L.codag_get_input_staging.argtypes = [i32]
         L.codag_get_input_staging.restype = i32
+        L.codag_set_deflate_pool_limit.argtypes = [u64]
+        L.codag_get_deflate_pool_limit.restype = u64
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
                      "codag_decompress_host",
                      "codag_last_chunk_status", "codag_batch_graph_create",
@@ -245,6 +247,15 @@ def codag_set_input_staging(fmt, mode: int):
 
 def codag_get_input_staging(fmt) -> int:
     return lib().codag_get_input_staging(_fmt(fmt))
+
+
+def codag_set_deflate_pool_limit(nbytes: int):
+    """Bound on the two-pass Deflate command pool in bytes (0: none)."""
+    _check(lib().codag_set_deflate_pool_limit(int(nbytes)), "codag_set_deflate_pool_limit")
+
+
+def codag_get_deflate_pool_limit() -> int:
+    return lib().codag_get_deflate_pool_limit()
 
 
 def codag_get_parts_per_chunk() -> int:

@@ -20,6 +20,7 @@ std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_batch_ctas_per_sm{0};
 std::atomic<int> g_parts_per_chunk{0};
 std::atomic<int> g_reg_ring[8];  // per decoder family: 1 = register staging ring
+std::atomic<uint64_t> g_pool_limit{0};  // Deflate command pool bound in bytes (0: none)
 
 codag_status fail(codag_status s, const std::string& msg) {
   g_last_error = msg;
@@ -39,11 +40,9 @@ constexpr uint64_t kSliceBytes = 16ull << 20;
 constexpr int kMaxSlices = 64;
 constexpr int kPipeDecode = 4;
 
-// Two-pass Deflate command pool: words per chunk at first (a 64 KiB chunk
-// of any content fits), the most per chunk, and the most in all.
-constexpr uint32_t kHufCapInit = 16384;
-constexpr uint32_t kHufCapMax = 1u << 22;
-constexpr uint64_t kHufPoolMaxWords = 1ull << 30;
+// Two-pass Deflate command pool: its first size in words (enough for about
+// 64 MiB of output), grown to what an earlier call needed.
+constexpr uint64_t kHufPoolInitWords = 1ull << 24;
 struct HostPipe {
   cudaStream_t h2d = nullptr, d2h = nullptr;
   cudaStream_t dec[kPipeDecode] = {};
@@ -73,14 +72,13 @@ struct Workspace {
   // sizes: their register counts differ), family (1, 2, 4) and warps per CTA
   // (1..16); 0 = not known yet, -1 = unknown
   mutable int rle_avail[2][5][17] = {};
-  // two-pass Deflate: the copy-command pool (hcap words per chunk), the
-  // per-chunk command counts, chunk-claim counters (one per concurrent slice
-  // of codag_decompress_host, one for plain calls), and the largest command
-  // count the decoder has seen (a device word, copied to pinned host memory
-  // after each call; the next call sizes its pool from it)
+  // two-pass Deflate: the copy-command pool, the per-chunk command counts,
+  // chunk-claim counters (one per concurrent slice of codag_decompress_host,
+  // one for plain calls), and the pool size the last call needed (a device
+  // word, copied to pinned host memory after each call; the next call sizes
+  // its pool from it)
   uint32_t* hcmd = nullptr;
   uint64_t hcmd_words = 0;
-  uint32_t hcap = kHufCapInit;
   uint32_t* hncmd = nullptr;
   uint64_t hncmd_cap = 0;
   uint32_t* hctr = nullptr;
@@ -185,18 +183,18 @@ codag_status check_common(const void* comp, const uint64_t* comp_offsets, uint64
 
 // One launch's share of the two-pass Deflate scratch.
 struct DeflateRun {
-  uint32_t* cmd = nullptr;  // the launch's first chunk's command slot
-  uint32_t cap = 0;         // command words per chunk
+  uint32_t* cmd = nullptr;  // the launch's part of the command pool
+  uint64_t pool_words = 0;  // its size
   uint32_t* ncmd = nullptr; // the launch's first chunk's count
   uint32_t* counter = nullptr;
   unsigned long long* need = nullptr;
 };
 
 // Size the two-pass Deflate scratch for a call of n chunks (store: with the
-// command pool).  The per-chunk capacity grows to what an earlier call
-// needed (plus an eighth); a chunk that still does not fit is decoded by the
-// one-warp decoder instead, so the capacity is a speed setting only.
-codag_status deflate_prepare(Workspace& w, uint64_t n, bool store, uint32_t* cap_out) {
+// command pool).  The pool grows to what an earlier call needed (plus a
+// quarter); a chunk whose region lies past it is decoded by the one-warp
+// decoder instead, so the pool size is a speed setting only.
+codag_status deflate_prepare(Workspace& w, uint64_t n, bool store, uint64_t known_words = 0) {
   if (!w.hctr) {
     if (cudaMalloc(&w.hctr, (kMaxSlices + 1) * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&w.hneed, sizeof(unsigned long long)) != cudaSuccess ||
@@ -207,16 +205,12 @@ codag_status deflate_prepare(Workspace& w, uint64_t n, bool store, uint32_t* cap
     }
     *w.hneed_host = 0;
   }
-  *cap_out = 0;
   if (!store) return CODAG_OK;
-  const unsigned long long need = *reinterpret_cast<volatile unsigned long long*>(w.hneed_host);
-  if (need > w.hcap) {
-    const unsigned long long want = (need + need / 8 + 255) & ~255ull;
-    w.hcap = want > kHufCapMax ? kHufCapMax : (uint32_t)want;
-  }
-  uint64_t cap = w.hcap;
-  if (n * cap > kHufPoolMaxWords) cap = kHufPoolMaxWords / n;
-  const uint64_t words = n * cap;
+  const unsigned long long need =
+      known_words ? known_words : *reinterpret_cast<volatile unsigned long long*>(w.hneed_host);
+  uint64_t words = need > kHufPoolInitWords ? need : kHufPoolInitWords;
+  const uint64_t limit = g_pool_limit.load() / sizeof(uint32_t);
+  if (limit && words > limit) words = limit;
   if (words > w.hcmd_words) {
     if (w.hcmd) cudaFree(w.hcmd);
     w.hcmd = nullptr;
@@ -239,16 +233,21 @@ codag_status deflate_prepare(Workspace& w, uint64_t n, bool store, uint32_t* cap
     }
     w.hncmd_cap = alloc;
   }
-  *cap_out = (uint32_t)cap;
   return CODAG_OK;
 }
 
 // The scratch of chunks [first, first + n) of a prepared call, claimed
-// through counter `slot` (0 .. kMaxSlices).
-DeflateRun deflate_run(const Workspace& w, uint32_t cap, uint64_t first, int slot) {
+// through counter `slot` (0 .. kMaxSlices); region: the pool word where
+// chunk `first`'s region starts (its output offset from the call's first
+// chunk / 4 + 2 first), so that slices decoded at the same time never share
+// pool words.
+DeflateRun deflate_run(const Workspace& w, uint64_t region, uint64_t first, int slot) {
   DeflateRun r;
-  r.cap = cap;
-  r.cmd = w.hcmd ? w.hcmd + first * cap : nullptr;
+  uint64_t words = w.hcmd_words;
+  const uint64_t limit = g_pool_limit.load() / sizeof(uint32_t);
+  if (limit && words > limit) words = limit;
+  r.cmd = w.hcmd ? w.hcmd + (region < words ? region : words) : nullptr;
+  r.pool_words = w.hcmd && region < words ? words - region : 0;
   r.ncmd = w.hncmd ? w.hncmd + first : nullptr;
   r.counter = w.hctr + slot;
   r.need = w.hneed;
@@ -281,9 +280,8 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
   if ((s = grow_status(*w, n)) != CODAG_OK) return s;
   w->last_n = n;
   if (fam == 3) {
-    uint32_t cap;
-    if ((s = deflate_prepare(*w, n, store, &cap)) != CODAG_OK) return s;
-    const DeflateRun dr = deflate_run(*w, cap, 0, kMaxSlices);
+    if ((s = deflate_prepare(*w, n, store)) != CODAG_OK) return s;
+    const DeflateRun dr = deflate_run(*w, 0, 0, kMaxSlices);
     s = launch_kernel(*w, format, comp, comp_offsets, n, out, out_offsets, sizes, store, w->status,
                       stream, &dr);
     if (s == CODAG_OK && store) {
@@ -360,7 +358,7 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
   if (fam == 3 && !reg && dr) {
     // two passes: Huffman decoding a lane per chunk, then the copies a warp
     // per chunk, then the one-warp decoder for chunks left to it
-    HufArgs h{dr->cmd, dr->cap, dr->ncmd, dr->counter, dr->need};
+    HufArgs h{dr->cmd, dr->pool_words, dr->ncmd, dr->counter, dr->need};
     cudaError_t e = cudaMemsetAsync(dr->counter, 0, sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     const uint64_t lanes = 32ull * kHufWarps;
@@ -578,13 +576,18 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
   HostPipe& p = w->pipe;
   if ((s = init_pipe(p)) != CODAG_OK) return s;
   if ((s = grow_offs(p, 2 * (n + 1))) != CODAG_OK) return s;
-  uint32_t hcap = 0;
-  if (family_of(format) == 3 && (s = deflate_prepare(*w, n, true, &hcap)) != CODAG_OK) return s;
+  // the pool this call needs is known here from the host offsets
+  if (family_of(format) == 3 &&
+      (s = deflate_prepare(*w, n, true, (h_out_offsets[n] - h_out_offsets[0]) / 4 + 2 * n + 2)) != CODAG_OK)
+    return s;
   w->last_n = n;
-  // a Deflate or byte RLE decoder is one warp (about 40 resident per SM), an RLE decoder
-  // a CTA (a few per SM)
-  const uint64_t min_chunks =
-      (uint64_t)w->sm_count * (family_of(format) >= 3 ? 40 : 8) / kPipeDecode;
+  // decoders resident per SM: a Deflate chunk is one lane of the Huffman
+  // pass (32 * kHufWarps per SM), a byte RLE or ORC zlib chunk one warp
+  // (about 40), an RLE chunk a CTA (a few); kPipeDecode slices in flight
+  // should fill them
+  const int fam = family_of(format);
+  const uint64_t per_sm = fam == 3 ? 32 * kHufWarps : fam >= 4 ? 40 : 8;
+  const uint64_t min_chunks = (uint64_t)w->sm_count * per_sm / kPipeDecode;
   const std::vector<uint64_t> bounds = plan_slices(h_out_offsets, n, min_chunks);
   uint64_t* d_coff = p.offs;
   uint64_t* d_ooff = p.offs + (n + 1);
@@ -618,7 +621,7 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
     if (e == cudaSuccess) e = cudaEventRecord(p.copied[k], p.h2d);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, p.copied[k], 0);
     if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy in");
-    const DeflateRun dr = deflate_run(*w, hcap, a, (int)k);
+    const DeflateRun dr = deflate_run(*w, (h_out_offsets[a] - h_out_offsets[0]) / 4 + 2 * a, a, (int)k);
     s = launch_kernel(*w, format, d_comp, d_coff + a, b - a, d_out, d_ooff + a, nullptr, true,
                       w->status + a, ds, family_of(format) == 3 ? &dr : nullptr);
     if (s != CODAG_OK) return s;
@@ -813,6 +816,13 @@ int codag_get_input_staging(int format) {
   const int fam = family_of(format);
   return (fam == 3 || fam == 4) ? g_reg_ring[fam].load() : -1;
 }
+
+codag_status codag_set_deflate_pool_limit(uint64_t bytes) {
+  g_pool_limit.store(bytes);
+  return CODAG_OK;
+}
+
+uint64_t codag_get_deflate_pool_limit(void) { return g_pool_limit.load(); }
 
 uint64_t codag_kernel_launches(void) { return g_launches.load(); }
 

@@ -30,8 +30,13 @@
 //                  block's input offset is parked in its first four output
 //                  bytes (stored blocks of fewer than 4 bytes are literals);
 //   - every check of the serial decoder is made here, in stream order, so a
-//     chunk's status is final after this pass; a chunk whose commands do not
-//     fit its slot of the command pool is marked kDeferred and decoded later
+//     chunk's status is final after this pass;
+//   - chunk c's commands go to its region of the command pool, a quarter of
+//     a word per byte of its output span plus two (words
+//     [U_c / 4 + 2 c, U_{c+1} / 4 + 2 c + 2) with U_c the output offset from
+//     the launch's first chunk), so chunks with disjoint output spans never
+//     share pool words; a chunk whose commands do not fit its region, or
+//     whose region is past the pool, is marked kDeferred and decoded later
 //     by the one-warp decoder (inflate.cuh).
 //
 // Pass 2, inflate_lz77_kernel (one warp per chunk, many warps per SM): the
@@ -265,14 +270,19 @@ struct LaneIn {
   }
 };
 
-// Pool of copy commands: chunk c (of this launch) owns words [c * cap, c * cap + cap).
+// The command pool of a launch and its bookkeeping.
 struct HufArgs {
-  uint32_t* cmd;        // command pool
-  uint32_t cap;         // command words per chunk
+  uint32_t* cmd;        // command pool (this launch's part)
+  uint64_t pool_words;  // its size in words
   uint32_t* ncmd;       // per chunk: commands written
   uint32_t* counter;    // chunk claims, zeroed before the launch
-  unsigned long long* need;  // largest command count seen (atomic max; a hint for the host)
+  unsigned long long* need;  // pool words the launch needs (atomic max; a hint for the host)
 };
+
+// Start of chunk c's command region (see the file header).
+__device__ __forceinline__ uint64_t cmd_region(const Args& a, uint64_t c) {
+  return (a.out_off[c] - a.out_off[0]) / 4 + 2 * c;
+}
 
 enum : uint32_t { LS_NEED_CHUNK = 0, LS_NEED_HEADER = 1, LS_IN_BLOCK = 2, LS_GONE = 3 };
 
@@ -317,12 +327,7 @@ struct LaneDec {
     if (STORE && st == ST_OK) {
       if (run) emit_cmd(0x80000000u | run);
       run = 0;
-      if (ncmd > ccap) {
-        atomicMax(h->need, 2ull * ccap);
-        st = kDeferred;
-      } else {
-        atomicMax(h->need, (unsigned long long)ncmd);
-      }
+      if (ncmd > ccap) st = kDeferred;
       h->ncmd[c] = ncmd;
     }
     a->status[c] = st;
@@ -343,7 +348,7 @@ struct LaneDec {
     run = 0;
     ncmd = 0;
     stuck = false;
-    ccap = h->cap;
+    ccap = 0;
     cap = 0xffffffffu;
     if (ce < cs || ce > total) {
       finish(ST_BAD_SPAN);
@@ -362,7 +367,21 @@ struct LaneDec {
       }
       cap = (uint32_t)(oe - os);
       out = a->out + os;
-      cmd = h->cmd + c * (uint64_t)h->cap;
+      // the region of a chunk with a valid span; one past the pool (or an
+      // output start before the launch's first) leaves the chunk to the
+      // one-warp decoder
+      const uint64_t o0 = a->out_off[0];
+      if (os < o0) {
+        finish(kDeferred);
+        return;
+      }
+      const uint64_t r0 = cmd_region(*a, c), r1 = (oe - o0) / 4 + 2 * c + 2;
+      if (r1 > h->pool_words) {
+        finish(kDeferred);
+        return;
+      }
+      cmd = h->cmd + r0;
+      ccap = (uint32_t)((r1 - r0) < 0xffffffffull ? r1 - r0 : 0xffffffffull);
     }
     if (n_in >= (1ull << 29)) {
       finish(ST_BAD_SPAN);
@@ -643,6 +662,8 @@ __device__ void huffman_body(const Args& a, const HufArgs& h) {
   extern __shared__ __align__(128) uint8_t smem[];
   HufCta* F = reinterpret_cast<HufCta*>(smem + kHufWarps * sizeof(LaneTables));
   huf_cta_init(F);
+  if (STORE && blockIdx.x == 0 && threadIdx.x == 0)  // the pool this launch needs, for the next call
+    atomicMax(h.need, (unsigned long long)((a.out_off[a.n] - a.out_off[0]) / 4 + 2 * a.n + 2));
   __syncthreads();
   LaneDec<STORE> s;
   s.a = &a;
@@ -694,7 +715,7 @@ __device__ __forceinline__ void lz77_chunk(const Args& a, const HufArgs& h, uint
   const uint32_t n_in = (uint32_t)(a.comp_off[c + 1] - cs);
   uint8_t* out = a.out + os;
   const uint8_t* in = a.comp + cs;
-  const uint32_t* cmd = h.cmd + c * (uint64_t)h.cap;
+  const uint32_t* cmd = h.cmd + cmd_region(a, c);
   const uint32_t ncmd = h.ncmd[c];
   uint32_t opos = 0;
   for (uint32_t g = 0; g < ncmd; g += 32) {

@@ -95,6 +95,14 @@ def test_input_staging_setting():
         assert L.codag_get_input_staging(f) == 0
 
 
+def test_deflate_pool_limit_setting():
+    assert codag.codag_get_deflate_pool_limit() == 0  # default: no bound
+    codag.codag_set_deflate_pool_limit(1 << 20)
+    assert codag.codag_get_deflate_pool_limit() == 1 << 20
+    codag.codag_set_deflate_pool_limit(0)
+    assert codag.codag_get_deflate_pool_limit() == 0
+
+
 def test_python_binding_names_match_abi():
     for name in declared_functions():
         if name in ("codag_last_error",):

@@ -30,6 +30,13 @@ def test_full_column(name):
     autotune.apply(n_chunks=None, family=name)
     try:
         got, st = run_plain(fmt, w.comp, w.comp_off, w.out_off)
+        if name == "deflate":
+            # the first call may leave chunks past the Deflate command pool to
+            # the one-warp decoder (the pool then grows to this call's need);
+            # the benchmark times later calls, where the two passes take all
+            assert (st == 0).all()
+            assert_parity(fmt, w.comp, w.comp_off, w.out_off, got, st, threads=THREADS)
+            got, st = run_plain(fmt, w.comp, w.comp_off, w.out_off)
     finally:
         codag.codag_set_parts_per_chunk(0)
         codag.codag_set_batch_ctas_per_sm(0)

@@ -18,6 +18,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 from devutil import assert_parity, pack, run_batch, run_plain, run_sizes  # noqa: E402
+import paper_2307_03760_gb300 as codag  # noqa: E402
 
 RLE_FMTS = [1, 2, 4, 5]
 ALL_FMTS = [1, 2, 3, 4, 5]
@@ -67,6 +68,28 @@ def test_workload_parity_small(fmt, parts):
     assert (st == 0).all()
     assert np.array_equal(got, w.plain)
     assert_parity(fmt, w.comp, w.comp_off, w.out_off, got, st)
+
+
+@pytest.mark.parametrize("limit", [64 << 10, 1 << 20])
+def test_deflate_pool_bound_fallback(limit):
+    """A bounded command pool leaves the chunks past it to the one-warp
+    decoder in the same call: every chunk must still match the oracle, for
+    valid and for corrupted chunks."""
+    sizes = [65536] * 12 + [1, 100, 4097, 70000, 131072, 300000]
+    w = synth.build_chunks([3] * len(sizes), sizes, seed=41, keep_plain=True)
+    comp = w.comp.copy()
+    rng = np.random.default_rng(9)
+    for c in range(2, w.n, 4):
+        a, b = int(w.comp_off[c]), int(w.comp_off[c + 1])
+        if b - a > 8:
+            comp[rng.integers(a + 4, b)] ^= 0x21
+    codag.codag_set_deflate_pool_limit(limit)
+    try:
+        got, st = run_plain(3, comp, w.comp_off, w.out_off)
+    finally:
+        codag.codag_set_deflate_pool_limit(0)
+    assert_parity(3, comp, w.comp_off, w.out_off, got, st)
+    assert (st == 0).sum() >= w.n // 2
 
 
 @pytest.mark.parametrize("shift", [1, 3, 8, 15])
