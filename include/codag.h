@@ -326,6 +326,21 @@ int codag_get_input_staging(int format);
 codag_status codag_set_deflate_pool_limit(uint64_t bytes);
 uint64_t codag_get_deflate_pool_limit(void);
 
+/*
+ * codag_set_wait_limit_ns - bound, in nanoseconds, of every device wait on
+ * work in progress: a staging copy a decoder needs next, or a segment start
+ * another warp of the chunk publishes.  Default 100 ms (100000000); 0 makes
+ * such a wait give up unless it is already complete.  A wait that runs out
+ * ends the chunk with CODAG_CHUNK_TIMEOUT (no other status), after the
+ * decoder has waited, bounded by the default, for its own copies in flight.
+ * For tests of that path and for callers that prefer a bounded stall; the
+ * library's addition, the paper has none.  Process-wide; applies to calls
+ * enqueued after it returns (do not call it while decodes are in flight).
+ * Returns CODAG_ECUDA if the value cannot be set on the current device.
+ */
+codag_status codag_set_wait_limit_ns(uint64_t ns);
+uint64_t codag_get_wait_limit_ns(void);
+
 /* Number of kernel launches the library enqueued since load (all calls). */
 uint64_t codag_kernel_launches(void);
 

@@ -78,6 +78,8 @@ def lib() -> ctypes.CDLL:
         L.codag_get_input_staging.restype = i32
         L.codag_set_deflate_pool_limit.argtypes = [u64]
         L.codag_get_deflate_pool_limit.restype = u64
+        L.codag_set_wait_limit_ns.argtypes = [u64]
+        L.codag_get_wait_limit_ns.restype = u64
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
                      "codag_decompress_host",
                      "codag_last_chunk_status", "codag_batch_graph_create",
@@ -256,6 +258,15 @@ def codag_set_deflate_pool_limit(nbytes: int):
 
 def codag_get_deflate_pool_limit() -> int:
     return lib().codag_get_deflate_pool_limit()
+
+
+def codag_set_wait_limit_ns(ns: int):
+    """Bound of device waits on work in progress (default 100 ms; 0: no wait)."""
+    _check(lib().codag_set_wait_limit_ns(int(ns)), "codag_set_wait_limit_ns")
+
+
+def codag_get_wait_limit_ns() -> int:
+    return lib().codag_get_wait_limit_ns()
 
 
 def codag_get_parts_per_chunk() -> int:

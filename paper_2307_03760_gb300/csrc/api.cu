@@ -21,6 +21,7 @@ std::atomic<int> g_batch_ctas_per_sm{0};
 std::atomic<int> g_parts_per_chunk{0};
 std::atomic<int> g_reg_ring[8];  // per decoder family: 1 = register staging ring
 std::atomic<uint64_t> g_pool_limit{0};  // Deflate command pool bound in bytes (0: none)
+std::atomic<uint64_t> g_wait_limit{100ull * 1000 * 1000};  // work-wait bound of the kernels, ns
 
 codag_status fail(codag_status s, const std::string& msg) {
   g_last_error = msg;
@@ -816,6 +817,21 @@ int codag_get_input_staging(int format) {
   const int fam = family_of(format);
   return (fam == 3 || fam == 4) ? g_reg_ring[fam].load() : -1;
 }
+
+codag_status codag_set_wait_limit_ns(uint64_t ns) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  Workspace* w;
+  codag_status s = current_ws(&w);  // the kernels' modules are loaded
+  if (s != CODAG_OK) return s;
+  cudaError_t e = set_wait_limit_rle(ns);
+  if (e == cudaSuccess) e = set_wait_limit_inflate(ns);
+  if (e == cudaSuccess) e = set_wait_limit_batch(ns);
+  if (e != cudaSuccess) return cuda_fail(e, "wait limit");
+  g_wait_limit.store(ns);
+  return CODAG_OK;
+}
+
+uint64_t codag_get_wait_limit_ns(void) { return g_wait_limit.load(); }
 
 codag_status codag_set_deflate_pool_limit(uint64_t bytes) {
   g_pool_limit.store(bytes);

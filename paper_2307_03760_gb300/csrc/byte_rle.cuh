@@ -91,27 +91,32 @@ __device__ __forceinline__ PartResult byte_rle_decode(In& in, int64_t n_in, bool
 // its control byte alone, so the walk reads one byte per group.  Lenient like
 // rle_v1_walk_staged: it does not check that a group's bytes are present.
 template <class In>
-__device__ __forceinline__ void byte_rle_walk(In& in, int64_t n_in, const uint64_t* target, int nsplit,
+__device__ __forceinline__ bool byte_rle_walk(In& in, int64_t n_in, const uint64_t* target, int nsplit,
                                               int64_t* split_pos, uint64_t* split_cnt,
                                               volatile uint32_t* published = nullptr) {
   int64_t pos = 0;
   uint64_t count = 0;
   int k = 1;
   uint64_t tk = target[1];
+  bool waited_out = false;  // a staging wait ran out: the splits are not usable
   while (pos < n_in) {
     if (count >= tk) {
       do {
         publish_split(k, pos, count, split_pos, split_cnt, published);
-        if (++k > nsplit) return;
+        if (++k > nsplit) return true;
         tk = target[k];
       } while (count >= tk);
     }
-    if (!in.ensure(pos, pos + 1)) break;
+    if (!in.ensure(pos, pos + 1)) {
+      waited_out = true;
+      break;
+    }
     const int h = (int8_t)in.byte(pos);
     count += h >= 0 ? (uint32_t)h + 3 : (uint32_t)(-h);
     pos += h >= 0 ? 2 : 1 - h;
   }
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+  return !waited_out;
 }
 
 }  // namespace codag

@@ -83,20 +83,23 @@ __device__ __forceinline__ PartResult decode_rle_part(In& in, uint8_t* scratch, 
   return r;
 }
 
-// Walk a chunk (one warp) to the start of part k: returns (position, count).
+// Walk a chunk (one warp) to the start of part k: returns (position, count),
+// and false when a staging wait ran out on the way.
 template <int FAMILY, class In>
-__device__ __forceinline__ void walk_to(In& in, uint8_t* scratch, int64_t n_in, uint64_t target,
+__device__ __forceinline__ bool walk_to(In& in, uint8_t* scratch, int64_t n_in, uint64_t target,
                                         int64_t* pos, uint64_t* count) {
   uint64_t t[2] = {0, target};
   int64_t sp[2];
   uint64_t sc[2];
+  bool ok;
   if (FAMILY == 1)
-    rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), n_in, t, 1, sp, sc);
+    ok = rle_v1_walk(in, reinterpret_cast<uint16_t*>(scratch), n_in, t, 1, sp, sc);
   else
-    rle_v2_walk(in, n_in, t, 1, sp, sc);
+    ok = rle_v2_walk(in, n_in, t, 1, sp, sc);
   // every lane computed the same values; lane 0 stored them
   *pos = (int64_t)shfl64((uint64_t)sp[1], 0);
   *count = shfl64(sc[1], 0);
+  return ok;
 }
 
 // Part k of K of chunk c through a per-warp staging ring (batch kernel): the
@@ -121,23 +124,28 @@ __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, 
     const uint64_t cap_v = g.cap / 8;
     int64_t base = 0;
     uint64_t count0 = 0;
-    if (k > 0) walk_to<FAMILY>(ring, scratch, g.n_in, part_target(cap_v, k, K), &base, &count0);
+    bool walked = true;
+    if (k > 0) walked = walk_to<FAMILY>(ring, scratch, g.n_in, part_target(cap_v, k, K), &base, &count0);
     const uint64_t hi = (k + 1 < K) ? part_target(cap_v, k + 1, K) : ~0ull;
-    r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, g, format, base, count0, hi);
+    if (walked) r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, g, format, base, count0, hi);
+    else r = PartResult{ST_TIMEOUT, 0, 0};
   }
   // bounded wait for this warp's own copies still in flight, also after a timeout
   if (!ring.drain()) r.status = ST_TIMEOUT;
   return r;
 }
 
-// Wait (bounded) until at least k + 1 segment starts are published.
+// Wait (bounded by work_wait_ns()) until at least k + 1 segment starts are
+// published.
 __device__ __forceinline__ bool wait_published(volatile uint32_t* published, uint32_t k) {
   if (*published > k) return true;
+  const uint64_t limit = work_wait_ns();
+  if (limit == 0) return false;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t polls = 0; polls < kMaxWaitPolls; polls++) {
     __nanosleep(128);
     if (*published > k) return true;
-    if (globaltimer_ns() - t0 > kMaxWaitNs) return false;
+    if (globaltimer_ns() - t0 > limit) return false;
   }
   return false;
 }
@@ -224,8 +232,10 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
       }
       if (lane_id() < tail) stage[bulk + lane_id()] = __ldg(gsrc + bulk + lane_id());
     }
-    bool ok = mbar_wait_bounded(bar, 0);
-    if (!ok) ok = mbar_wait_bounded(bar, 0);  // second bounded wait for the copies in flight
+    bool ok = mbar_wait_bounded(bar, 0, work_wait_ns());
+    // a wait that ran out still waits (kMaxWaitNs) for the copies in flight
+    // before the CTA stops; the chunk reports TIMEOUT either way
+    if (!ok) mbar_wait_bounded(bar, 0);
     ok = __syncthreads_and(ok);  // CTA-uniform; also publishes warp 0's tail bytes
     StagedInput in{stage, gsrc, skew};
     V1Bitmap vb{nullptr, (uint32_t)skew, 0};
@@ -290,24 +300,28 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     if (warp == 0 && K > 1) {
       ring.start(chunk, g.n_in, buf_end);
       if (FAMILY == 1)
-        rle_v1_walk(ring, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
-                    split_pos, split_cnt);
+        ok = rle_v1_walk(ring, reinterpret_cast<uint16_t*>(scratch), g.n_in, target, (int)K - 1,
+                         split_pos, split_cnt);
       else if (FAMILY == 4)
-        byte_rle_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
+        ok = byte_rle_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
       else
-        rle_v2_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
-      ok = ring.drain();
+        ok = rle_v2_walk(ring, g.n_in, target, (int)K - 1, split_pos, split_cnt);
+      ok = ring.drain() && ok;
     }
-    __syncthreads();
+    // a walk whose wait ran out leaves unusable splits: the chunk times out
+    ok = __syncthreads_and(ok);
     // this part's sub-stream, through a ring started at its first byte
-    const int64_t base = split_pos[warp];
-    ChunkGeom sub = g;
-    sub.n_in = g.n_in - base;
-    ring.start(chunk + base, sub.n_in, buf_end);
-    const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
-    PartResult r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, sub, a.format, 0, split_cnt[warp], hi);
-    if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
-    if (!ring.drain() || !ok) r.status = ST_TIMEOUT;
+    PartResult r{ST_TIMEOUT, 0, 0};
+    if (ok) {
+      const int64_t base = split_pos[warp];
+      ChunkGeom sub = g;
+      sub.n_in = g.n_in - base;
+      ring.start(chunk + base, sub.n_in, buf_end);
+      const uint64_t hi = warp + 1 < K ? target[warp + 1] : ~0ull;
+      r = decode_rle_part<FAMILY, STORE>(ring, scratch, a, sub, a.format, 0, split_cnt[warp], hi);
+      if (r.status != ST_OK && r.status != ST_TIMEOUT) r.err_pos += base;
+      if (!ring.drain()) r.status = ST_TIMEOUT;
+    }
     if (lane_id() == 0 && r.status != ST_OK) atomicMin(key, status_key(r));
     if (!STORE && warp == K - 1 && lane_id() == 0) a.sizes[c] = r.count;
   }

@@ -170,21 +170,53 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Test a phase without waiting.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounds on one mbarrier phase wait before the decoder gives up on the chunk
 // (ST_TIMEOUT): wall time, and a poll count in case the timer stalls.  A TMA
 // copy of at most a few KiB completes in microseconds.
 constexpr uint64_t kMaxWaitNs = 100ull * 1000 * 1000;  // 100 ms
 constexpr uint32_t kMaxWaitPolls = 1u << 20;
 
-// Wait for `parity` of `bar`; false if the bounded wait ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bound of a wait on work in progress (a copy the decoder needs next, a
+// segment start another warp publishes): kMaxWaitNs unless
+// codag_set_wait_limit_ns shortens it (0: give up unless already complete),
+// so that tests can make such waits run out.  A decoder's wait for its own
+// copies in flight before it stops always uses kMaxWaitNs.  One copy per
+// translation unit, set through set_wait_limit_here().
+static __device__ uint64_t g_wait_limit_ns = kMaxWaitNs;
+
+__device__ __forceinline__ uint64_t work_wait_ns() {
+  return *reinterpret_cast<volatile uint64_t*>(&g_wait_limit_ns);
+}
+
+// Wait for `parity` of `bar` for at most limit_ns; false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kMaxWaitNs) {
+  if (limit_ns == 0) return mbar_test(bar, parity);
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t polls = 0; polls < kMaxWaitPolls; polls++) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (globaltimer_ns() - t0 > kMaxWaitNs) return false;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
   }
   return false;
+}
+
+// Host: this translation unit's copy of the work-wait bound.
+static inline cudaError_t set_wait_limit_here(uint64_t ns) {
+  return cudaMemcpyToSymbol(g_wait_limit_ns, &ns, sizeof(ns));
 }
 
 }  // namespace codag

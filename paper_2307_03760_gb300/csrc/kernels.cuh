@@ -148,6 +148,12 @@ __global__ void batch_finalize_kernel(const uint8_t* formats, const uint64_t* co
                                       const uint64_t* out_off, uint64_t n,
                                       const unsigned long long* keys, int32_t* status);
 
+// Host: set the work-wait bound (codag_set_wait_limit_ns) in each unit that
+// has bounded device waits.
+cudaError_t set_wait_limit_rle(uint64_t ns);
+cudaError_t set_wait_limit_inflate(uint64_t ns);
+cudaError_t set_wait_limit_batch(uint64_t ns);
+
 // Dynamic shared memory of the batch kernel: per-warp regions + bucket tables.
 constexpr int kBatchSmem = kWarpsPerBlock * kBatchWarp + 2 * (kBuckets + 1) * 4;
 

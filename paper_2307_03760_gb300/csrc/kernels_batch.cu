@@ -104,4 +104,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(Args a) {
   }
 }
 
+// this unit's copy of the work-wait bound (codag_set_wait_limit_ns)
+cudaError_t set_wait_limit_batch(uint64_t ns) { return set_wait_limit_here(ns); }
+
 }  // namespace codag

@@ -26,4 +26,7 @@ __global__ void __launch_bounds__(kThreads) byte_rle_sizes_kernel(Args a) {
   warp_chunk_body<4, false, RleRing>(a);
 }
 
+// this unit's copy of the work-wait bound (codag_set_wait_limit_ns)
+cudaError_t set_wait_limit_inflate(uint64_t ns) { return set_wait_limit_here(ns); }
+
 }  // namespace codag

@@ -15,4 +15,7 @@ __global__ void __launch_bounds__(512) rle_v2_sizes_kernel(Args a) {
   rle_cta_body<2, false>(a, a.stage_bytes);
 }
 
+// this unit's copy of the work-wait bound (codag_set_wait_limit_ns)
+cudaError_t set_wait_limit_rle(uint64_t ns) { return set_wait_limit_here(ns); }
+
 }  // namespace codag

@@ -86,12 +86,15 @@ struct InRing {
     issued = k + 1;
   }
 
-  // Wait for slot `ready`; false if the bounded wait ran out.
-  __device__ __forceinline__ bool wait_next() {
+  // Wait for slot `ready`; false if the bounded wait ran out.  A wait for
+  // bytes the decoder needs is bounded by work_wait_ns(); the drain at the
+  // end of a chunk (own copies in flight) by kMaxWaitNs.
+  __device__ __forceinline__ bool wait_next(bool draining = false) {
     const uint32_t k = ready;
     const int s = k & (NSLOT - 1);
     if ((int64_t)k * SLOT < limit) {
-      if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u)) return false;
+      if (!mbar_wait_bounded(&bar[s], (parity >> s) & 1u, draining ? kMaxWaitNs : work_wait_ns()))
+        return false;
       parity ^= 1u << s;
     }
     ready = k + 1;
@@ -126,7 +129,7 @@ struct InRing {
   // Wait for every copy still in flight (end of a chunk).
   __device__ __forceinline__ bool drain() {
     while (ready < issued)
-      if (!wait_next()) return false;
+      if (!wait_next(true)) return false;
     __syncwarp();
     return true;
   }

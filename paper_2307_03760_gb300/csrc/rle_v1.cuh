@@ -275,27 +275,36 @@ __device__ __forceinline__ void publish_split(int k, int64_t pos, uint64_t count
 // Walk an RLE v1 stream's groups (one warp) and record where parts start;
 // same contract as rle_v2_walk.
 template <class In>
-__device__ __forceinline__ void rle_v1_walk(In& in, uint16_t* ends, int64_t n_in,
+__device__ __forceinline__ bool rle_v1_walk(In& in, uint16_t* ends, int64_t n_in,
                                             const uint64_t* target, int nsplit, int64_t* split_pos,
                                             uint64_t* split_cnt,
                                             volatile uint32_t* published = nullptr) {
   int64_t pos = 0;
   uint64_t count = 0;
   int k = 1;
+  bool waited_out = false;  // a staging wait ran out: the splits are not usable
   while (pos < n_in && k <= nsplit) {
     while (k <= nsplit && count >= target[k]) {
       publish_split(k, pos, count, split_pos, split_cnt, published);
       k++;
     }
     if (k > nsplit) break;
-    if (!in.ensure(pos, pos + 24)) break;
+    if (!in.ensure(pos, pos + 24)) {
+      waited_out = true;
+      break;
+    }
     V1Group gr;
-    if (v1_parse_group(in, pos, n_in, ends, gr) != ST_OK) break;
+    const int32_t st = v1_parse_group(in, pos, n_in, ends, gr);
+    if (st != ST_OK) {
+      waited_out = st == ST_TIMEOUT;
+      break;
+    }
     __syncwarp();
     count += gr.len;
     pos = gr.end;
   }
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+  return !waited_out;
 }
 
 // Walk of a staged chunk (one warp) with its terminator bitmap and rank

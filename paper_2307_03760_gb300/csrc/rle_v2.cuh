@@ -138,26 +138,32 @@ __device__ __forceinline__ int32_t v2_parse_run(const In& in, int64_t pos, int64
 // first value index is >= target[k].  Where the walk stops early (a header
 // error, or the end of the stream) the remaining splits get that position,
 // so the last part finds the error again.  split_pos / split_cnt: shared.
+// Returns false when a staging wait ran out (the splits are then unusable).
 template <class In>
-__device__ __forceinline__ void rle_v2_walk(In& in, int64_t n_in, const uint64_t* target,
+__device__ __forceinline__ bool rle_v2_walk(In& in, int64_t n_in, const uint64_t* target,
                                             int nsplit, int64_t* split_pos, uint64_t* split_cnt,
                                             volatile uint32_t* published = nullptr) {
   int64_t pos = 0;
   uint64_t count = 0;
   int k = 1;
+  bool waited_out = false;
   while (pos < n_in && k <= nsplit) {
     while (k <= nsplit && count >= target[k]) {
       publish_split(k, pos, count, split_pos, split_cnt, published);
       k++;
     }
     if (k > nsplit) break;
-    if (!in.ensure(pos, pos + 40)) break;
+    if (!in.ensure(pos, pos + 40)) {
+      waited_out = true;
+      break;
+    }
     V2Run r;
     if (v2_parse_run(in, pos, n_in, r) != ST_OK) break;
     count += r.len;
     pos = r.end;
   }
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
+  return !waited_out;
 }
 
 // Extent of the run at pos for the staged walk: its value count and end,

@@ -24,6 +24,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 ALIGN = 256
+# the library's call statuses that the serving loop reports (include/codag.h)
+CODAG_OK = 0
+CODAG_ETIMEOUT = 5
 
 
 class Arena:
@@ -81,6 +84,7 @@ class Request:
     t_done: float = -1.0
     status: np.ndarray | None = None
     rejected: bool = False
+    timed_out: bool = False  # not completed when the loop's deadline passed
     result: np.ndarray | None = None
 
     @property
@@ -186,11 +190,14 @@ class Stats:
     completed: int = 0
     rejected: int = 0
     batches: int = 0
+    timed_out: int = 0
+    status: int = CODAG_OK  # CODAG_ETIMEOUT when requests were left at the deadline
     wall: float = 0.0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies) if self.latencies else np.zeros(1)
         return {"completed": self.completed, "rejected": self.rejected, "batches": self.batches,
+                "timed_out": self.timed_out, "status": "ETIMEOUT" if self.status else "OK",
                 "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                 "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                 "mean_ms": round(float(lat.mean()) * 1e3, 3),
@@ -287,7 +294,10 @@ class Server:
     def run(self, requests: list[Request], pinned_inputs: dict, time_limit: float = 60.0):
         """Serve `requests` (their .arrival = seconds from start, sorted);
         returns Stats.  A request's latency is its completion time, as the
-        loop sees it, minus its arrival time."""
+        loop sees it, minus its arrival time.  The loop polls with a deadline:
+        at time_limit it stops waiting, marks every request not completed by
+        then timed_out, and returns Stats with status CODAG_ETIMEOUT (work
+        still in flight is left to drain())."""
         t0 = self.clock()
         nxt = 0
         pending = len(requests)
@@ -320,6 +330,12 @@ class Server:
                         self.ex.launch(slot, batch, pinned_inputs)
                         self.stats.batches += 1
         self.stats.wall = self.clock() - t0
+        if pending:
+            for r in requests:
+                if r.t_done < 0 and not r.rejected:
+                    r.timed_out = True
+                    self.stats.timed_out += 1
+            self.stats.status = CODAG_ETIMEOUT
         return self.stats
 
     def drain(self):

@@ -103,6 +103,10 @@ def test_deflate_pool_limit_setting():
     assert codag.codag_get_deflate_pool_limit() == 0
 
 
+def test_wait_limit_default():
+    assert codag.codag_get_wait_limit_ns() == 100_000_000
+
+
 def test_python_binding_names_match_abi():
     for name in declared_functions():
         if name in ("codag_last_error",):

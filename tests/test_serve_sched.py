@@ -7,8 +7,8 @@ import numpy as np
 
 import oracle
 import synth
-from paper_2307_03760_gb300.serve import (ALIGN, Arena, Request, Scheduler, Server, chunk_table,
-                                          comp_region)
+from paper_2307_03760_gb300.serve import (ALIGN, CODAG_ETIMEOUT, CODAG_OK, Arena, Request,
+                                          Scheduler, Server, chunk_table, comp_region)
 
 
 def _req(rid, w, arrival=0.0):
@@ -135,8 +135,37 @@ def test_serving_loop_continuous_batching_with_fake_executor():
     srv = Server(budget=1 << 20, streams=2, executor=ex, clock=tick, keep_results=True)
     stats = srv.run(reqs, inputs, time_limit=10.0)
     assert stats.completed == 30 and stats.rejected == 0
+    assert stats.status == CODAG_OK and stats.timed_out == 0
     assert any(len(b) > 1 for b in ex.launched)  # arrivals during a batch were batched together
     for r in reqs:
         assert (r.status == 0).all()
         assert np.array_equal(r.result, pool[r.rid % 3].plain)
         assert r.t_done >= r.arrival
+
+
+def test_serving_loop_deadline_returns_etimeout():
+    """Batches that never complete: the loop stops polling at its deadline,
+    reports CODAG_ETIMEOUT and marks exactly the unfinished requests."""
+    pool = [synth.build_chunks([2] * 2, [4096] * 2, 30, keep_plain=True)]
+    t = [0.0]
+
+    def tick():
+        t[0] += 0.001
+        return t[0]
+
+    ex = FakeExecutor(budget=1 << 20, streams=2, clock=tick, delay=0.004)
+    reqs = [Request(i, pool[0].formats, pool[0].comp, pool[0].comp_off, pool[0].out_off,
+                    arrival=0.0005 * i) for i in range(20)]
+    inputs = {r.rid: r.comp for r in reqs}
+    slow = ex.poll
+
+    def poll():  # batches launched after the first two never finish
+        return [d for d in slow() if min(r.rid for r in d[0]) < 2]
+
+    ex.poll = poll
+    srv = Server(budget=1 << 20, streams=2, executor=ex, clock=tick)
+    stats = srv.run(reqs, inputs, time_limit=0.2)
+    assert stats.status == CODAG_ETIMEOUT
+    assert stats.completed >= 1 and stats.timed_out == 20 - stats.completed
+    assert all(r.timed_out == (r.t_done < 0) for r in reqs)
+    assert stats.summary()["status"] == "ETIMEOUT"
