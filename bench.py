@@ -20,7 +20,10 @@ copy bandwidth.  ``cpu_baseline`` times the oracle (plain single-threaded C
 decoder per chunk, chunk ranges split over all host cores) on a bounded sample.
 
 Multi-GPU (torchrun): every rank decodes its own column (weak scaling, no
-collective on the data path); the step time is the max over ranks.
+collective on the data path); with ``--split`` the ranks instead decode
+contiguous chunk ranges of one column, balanced by compressed + decoded
+bytes (``shard.partition``; strong scaling).  The step time is the max over
+ranks.
 ``--impl reference`` times the oracle on the host cores instead (rank 0 only).
 """
 from __future__ import annotations
@@ -44,6 +47,7 @@ import synth  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 METRIC = "uncompressed GB/s per format on 1 GB300 and % of HBM roofline; p50/p99 request latency"
 
 
@@ -178,6 +182,56 @@ def time_steps(torch, stream, fn, steps: int, warmup: int):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def step_stats(ms):
+    """mean / median / p99 of per-step milliseconds."""
+    a = np.asarray(ms, dtype=np.float64)
+    return {"mean": round(float(a.mean()), 5), "p50": round(float(np.percentile(a, 50)), 5),
+            "p99": round(float(np.percentile(a, 99)), 5), "reps": int(a.size)}
+
+
+def _cudart():
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    return None
+
+
+def launch_overhead(torch, stream, reps: int = 500):
+    """Device time of one launch of an empty CUDA graph (the launch cost
+    alone), microseconds, median over `reps` replays timed with events."""
+    import ctypes
+    rt = _cudart()
+    if rt is None:
+        return None
+    g, e = ctypes.c_void_p(), ctypes.c_void_p()
+    if rt.cudaGraphCreate(ctypes.byref(g), ctypes.c_uint(0)) != 0:
+        return None
+    if rt.cudaGraphInstantiate(ctypes.byref(e), g, ctypes.c_ulonglong(0)) != 0:
+        rt.cudaGraphDestroy(g)
+        return None
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    fn = lambda: rt.cudaGraphLaunch(e, sh)  # noqa: E731
+    ms = time_steps(torch, stream, fn, reps, 10)
+    rt.cudaGraphExecDestroy(e)
+    rt.cudaGraphDestroy(g)
+    return round(1000.0 * float(np.median(ms)), 3)
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        fields = dict(line.split(":", 1) for line in out.splitlines() if ":" in line)
+        for key in ("Model name", "Vendor ID"):
+            if key in fields:
+                return " ".join(fields[key].split())
+    except Exception:
+        pass
+    return os.uname().machine
+
+
 def oracle_rate(w, fmt: int, seconds: float = 10.0, threads: int | None = None):
     """Oracle throughput (decoded GB/s) on a bounded sample: whole-column
     decodes split over `threads` host cores, repeated until `seconds`."""
@@ -299,14 +353,19 @@ def main():
     ap.add_argument("--no-per-format", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sweep")
-    ap.add_argument("--serve-seconds", type=float, default=1.0,
-                    help="arrival window per request rate in the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="arrival window per request rate in the serving sweep (at most 20,000 requests)")
+    ap.add_argument("--serve-payloads", type=int, default=128,
+                    help="distinct request payloads the serving sweep draws from")
     ap.add_argument("--parts", type=int, default=0,
                     help="parts per RLE chunk (0 = library default)")
     ap.add_argument("--no-tuning", action="store_true",
                     help="ignore the committed autotuner table")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="workload size factor; 1.0 is the measured configuration")
+    ap.add_argument("--split", action="store_true",
+                    help="ranks decode balanced ranges of one column (strong scaling) "
+                         "instead of a column each")
     args = ap.parse_args()
     global SCALE
     SCALE = args.scale
@@ -337,7 +396,15 @@ def main():
     peak, peak_kind = hbm_peak()
 
     name = args.workload
-    w = workload(name, 1 + rank)
+    if args.split:
+        from paper_2307_03760_gb300 import shard
+        whole = workload(name, 1)
+        first, last = shard.partition(whole.comp_off, whole.out_off, world)[rank]
+        w = slice_chunks(whole, first, last)
+        job_bytes = whole.out_bytes
+    else:
+        w = workload(name, 1 + rank)
+        job_bytes = world * w.out_bytes
     d = Dev(w, torch, dev)
 
     # arguments resolved once (raw pointers and stream handle), so that a step
@@ -373,14 +440,16 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    value = world * w.out_bytes * args.steps / (total_ms / 1e3) / 1e9
-    kernel_ms = statistics.mean(ms)  # one decode launch per step
+    value = job_bytes * args.steps / (total_ms / 1e3) / 1e9
+    kernel_ms = statistics.mean(ms)  # one decode launch per step (RLE)
     achieved = d.alg_bytes() / (kernel_ms / 1e3) / 1e9
     kernel = {"rle_v1": "rle_v1_kernel", "rle_v2": "rle_v2_kernel", "deflate": "inflate_kernel",
               "batched": "batch_kernel", "byte_rle": "byte_rle_cta_kernel",
               "bool_rle": "byte_rle_cta_kernel", "orc_zlib": "orc_zlib_kernel"}[name]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                "nominal_peak": NOMINAL_HBM_GBS,
                 "traffic": traffic_from_profile(kernel, w.n), "kernel": kernel,
                 "algorithmic_bytes_per_launch": d.alg_bytes()}
 
@@ -410,7 +479,7 @@ def main():
         t = torch.tensor([e2e_t], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_t = float(t.item())
-    e2e_val = world * w.out_bytes * len(e2e_ms) / (e2e_t / 1e3) / 1e9
+    e2e_val = job_bytes * len(e2e_ms) / (e2e_t / 1e3) / 1e9
     torch.cuda.synchronize()
     ok = np.array_equal(h_out[: w.out_bytes].numpy(), d.out[: w.out_bytes].cpu().numpy()) and \
         bool((h_status[: w.n].numpy() == 0).all())
@@ -418,12 +487,13 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong" if args.split else "weak", "vs_baseline": None,
         "dtype": "int64" if name in ("rle_v1", "rle_v2") else "u8", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC[name] + ("" if SCALE == 1.0 else f"_scaled_{SCALE}"), "chunks": w.n, "compressed_bytes": w.comp_bytes,
                    "uncompressed_bytes": w.out_bytes, "ratio": round(w.comp_bytes / w.out_bytes, 4),
                    "l2": "inputs+outputs larger than L2 (no flush)", "seed": 1,
-                   "parallelism": f"chunk-parallel x{world} (independent columns per GPU)",
+                   "parallelism": (f"chunk-parallel x{world} (one column split into balanced chunk ranges)"
+                                   if args.split else f"chunk-parallel x{world} (independent columns per GPU)"),
                    "parts_per_chunk": codag.codag_get_parts_per_chunk() or "auto",
                    "tuning": tuned},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s",
@@ -432,6 +502,8 @@ def main():
                 "api": "codag_decompress_batch between copies" if name == "batched"
                        else "codag_decompress_host (16 MiB slices, copies overlapped)"},
         "roofline": roofline,
+        "step_ms": step_stats(ms),
+        "launch_overhead_us": launch_overhead(torch, stream) if rank == 0 else None,
         "gpu_launches": int(gpu_launches),
         "clocks": clk.summary(),
     }
@@ -440,27 +512,33 @@ def main():
         line["per_format"] = per_format(torch, codag, dev, stream, peak, name, w, d, value, achieved)
 
     if rank == 0 and world == 1 and not args.no_serving:
-        line["serving"] = serving(torch, args.serve_seconds)
+        line["serving"] = serving(torch, args.serve_seconds, args.serve_payloads)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, threads, reps, el = oracle_rate(w, FMT_OF.get(name, 0), seconds=10.0)
+        # one core, on a slice of the column (about 3 s)
+        sub1 = slice_chunks(w, 0, max(1, w.n // 16))
+        rate1, _, reps1, el1 = oracle_rate(sub1, FMT_OF.get(name, 0), seconds=3.0, threads=1)
         line["cpu_baseline"] = {"value": round(rate, 3), "unit": "GB/s", "cores": threads,
-                                "kind": "oracle",
+                                "kind": "oracle", "cpu": cpu_model(),
                                 "sample": f"{reps} whole-column decode(s) of the same workload "
-                                          f"({w.out_bytes} bytes each) in {el:.1f} s"}
+                                          f"({w.out_bytes} bytes each) in {el:.1f} s",
+                                "single_thread": {"value": round(rate1, 3), "unit": "GB/s", "cores": 1,
+                                                  "sample": f"{reps1} decode(s) of the first {sub1.n} "
+                                                            f"chunks ({sub1.out_bytes} bytes) in {el1:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def serving(torch, seconds: float):
+def serving(torch, seconds: float, n_payloads: int = 128):
     """Continuous-batching server under Poisson arrivals: requests of 1-256
     chunks of one random format, 64 KiB-64 MiB decoded, 32 GiB HBM budget.
     Latency = arrival -> completion seen by the host, including the copy of
     the request's compressed bytes from pinned host memory."""
     from paper_2307_03760_gb300.serve import Request, Server
-    pool = synth.serving_pool(seed=1, n_payloads=32)
+    pool = synth.serving_pool(seed=1, n_payloads=n_payloads)
     pinned = [torch.from_numpy(w.comp).pin_memory() for w in pool]
     mean_bytes = float(np.mean([w.out_bytes for w in pool]))
     srv = Server(budget=32 << 30, streams=4, max_batch_chunks=32768)
@@ -476,10 +554,14 @@ def serving(torch, seconds: float):
         reqs = [Request(i, pool[p].formats, pool[p].comp, pool[p].comp_off, pool[p].out_off,
                         float(t)) for i, (t, p) in enumerate(zip(times, pick))]
         inputs = {r.rid: pinned[p] for r, p in zip(reqs, pick)}
-        st = srv.run(reqs, inputs, time_limit=seconds + 4.0)
+        window = float(times[-1]) if len(times) else seconds  # arrivals end here
+        # after the last arrival the loop drains: allow the offered bytes at 25 GB/s
+        offered = float(sum(pool[p].out_bytes for p in pick))
+        st = srv.run(reqs, inputs, time_limit=window + 4.0 + offered / 25e9)
         summ = st.summary()
         summ["offered_GBps"] = round(lam * mean_bytes / 1e9, 2)
         summ["requests"] = len(reqs)
+        summ["arrival_window_s"] = round(window, 3)
         summ["errors"] = int(sum(int((r.status != 0).any()) for r in reqs if r.status is not None))
         out["rates"][str(lam)] = summ
         srv.drain()
@@ -487,7 +569,8 @@ def serving(torch, seconds: float):
 
 
 def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
-    res = {headline: {"GBps": round(hvalue, 2), "hbm_frac": round(hach / peak, 4)}}
+    res = {headline: {"GBps": round(hvalue, 2), "hbm_frac": round(hach / peak, 4),
+                      "hbm_frac_of_nominal": round(hach / NOMINAL_HBM_GBS, 4)}}
     for name in ("rle_v1", "deflate", "byte_rle", "bool_rle", "orc_zlib"):
         if name == headline:
             continue
@@ -504,11 +587,14 @@ def per_format(torch, codag, dev, stream, peak, headline, hw, hd, hvalue, hach):
         fn()
         torch.cuda.synchronize()
         st = codag.codag_last_chunk_status(w.n)
-        ms = time_steps(torch, stream, fn, 10 if name in ("deflate", "orc_zlib") else 100, 3)
+        reps = 10 if name in ("deflate", "orc_zlib") else 400 if name == "rle_v1" else 100
+        ms = time_steps(torch, stream, fn, reps, 3)
         t = statistics.median(ms)
         res[name] = {"GBps": round(w.out_bytes / (t / 1e3) / 1e9, 2),
                      "hbm_frac": round(d.alg_bytes() / (t / 1e3) / 1e9 / peak, 4),
-                     "ms": round(t, 4), "chunks": w.n, "ratio": round(w.comp_bytes / w.out_bytes, 4),
+                     "hbm_frac_of_nominal": round(d.alg_bytes() / (t / 1e3) / 1e9 / NOMINAL_HBM_GBS, 4),
+                     "ms": round(t, 4), "step_ms": step_stats(ms),
+                     "chunks": w.n, "ratio": round(w.comp_bytes / w.out_bytes, 4),
                      "all_ok": bool((st == 0).all()), "workload": WORKLOAD_DESC[name]}
         del d
     codag.codag_set_parts_per_chunk(0)
