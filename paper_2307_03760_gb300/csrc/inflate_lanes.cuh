@@ -13,10 +13,12 @@
 // claim chunks from a global counter until none is left):
 //   - every lane owns interleaved shared-memory tables (element k of lane l
 //     at [k * 32 + l], so lanes that touch the same element index hit
-//     different banks): a 9-bit lit/len table and a 7-bit distance table,
+//     different banks): an 8-bit lit/len table and a 7-bit distance table,
 //     built by the lane itself per dynamic block (RFC 1951 Sec. 3.2.2); codes
 //     longer than the table index resolve through per-length limits; fixed
-//     blocks (Sec. 3.2.6) use one table pair per CTA;
+//     blocks (Sec. 3.2.6) use one table pair per CTA (9-bit lit/len index,
+//     so every fixed code is in the table).  The tables take 47 KB a warp,
+//     so 4 warps (128 chunks) fit per SM;
 //   - the lane reads its chunk from global memory through a four-word
 //     register queue (the next words are in flight while the current ones are
 //     decoded) into a 64-bit bit buffer;
@@ -49,13 +51,16 @@
 // over shuffles, at most five rounds.
 #pragma once
 
+#include <cstddef>
+
 #include "kernels.cuh"
 
 namespace codag {
 
-constexpr int kLaneLTB = 9;   // lit/len table index bits
+constexpr int kLaneLTB = 8;   // lit/len table index bits of a lane's (dynamic) code
+constexpr int kFixLTB = 9;    // lit/len table index bits of the fixed code (every code fits)
 constexpr int kLaneDTB = 7;   // distance (and code-length) table index bits
-constexpr int kHufWarps = 3;  // warps per CTA of the Huffman kernel
+constexpr int kHufWarps = 4;  // warps per CTA of the Huffman kernel (one CTA per SM)
 constexpr int kLz77Warps = 8;  // warps per CTA of the copy kernel
 
 // Table entry (16 bits): bits 0-3 code length, 4-12 value, 13-15 kind.
@@ -82,8 +87,11 @@ __device__ __forceinline__ uint32_t lane_sym_entry(int kind, uint32_t len, uint3
 
 // Per-warp shared memory: interleaved per-lane arrays.
 struct LaneTables {
-  uint16_t lit[(1 << kLaneLTB) * 32];  // also the lane's code lengths while a header is read
-  uint16_t dist[(1 << kLaneDTB) * 32];  // also the code-length code's table
+  // lit and dist, one after the other, also hold the lane's code lengths
+  // (up to 316) while a header is read; lsort then holds the code-length
+  // code's table
+  uint16_t lit[(1 << kLaneLTB) * 32];
+  uint16_t dist[(1 << kLaneDTB) * 32];
   uint16_t lsort[288 * 32];  // table entries of the symbols, in canonical order
   uint16_t dsort[32 * 32];
   uint16_t lmeta[2 * (15 - kLaneLTB) * 32];  // limits, then bases, of lengths LTB+1..15
@@ -92,7 +100,7 @@ struct LaneTables {
 // Per-CTA shared memory: the fixed codes' tables and the base values of
 // lengths and distances (RFC 1951 Sec. 3.2.5, 3.2.6).
 struct HufCta {
-  uint16_t flit[1 << kLaneLTB];
+  uint16_t flit[1 << kFixLTB];
   uint16_t fdist[1 << kLaneDTB];
   uint32_t len_base[32];
   uint32_t dist_base[32];
@@ -303,7 +311,8 @@ struct LaneDec {
   bool stuck;     // the fast step met a symbol it leaves to step()
   uint8_t* out;
   uint32_t* cmd;
-  const uint16_t* lt;  // lit/len table, element stride ls
+  const uint16_t* lt;  // lit/len table, element stride ls, index mask lm
+  uint32_t lm;
   const uint16_t* dt;  // distance table, element stride ds
   uint32_t ls, ds;
   LaneIn in;
@@ -408,6 +417,7 @@ struct LaneDec {
     if (btype == 0) return stored();
     if (btype == 1) {
       lt = F->flit;
+      lm = (1u << kFixLTB) - 1;
       dt = F->fdist;
       ls = ds = 1;
       state = LS_IN_BLOCK;
@@ -449,10 +459,17 @@ struct LaneDec {
     if (bfinal) finish(ST_OK);
   }
 
-  // RFC 1951 Sec. 3.2.7: code lengths, then the lane's own tables
+  // RFC 1951 Sec. 3.2.7: code lengths, then the lane's own tables.  The
+  // code lengths run through lit into dist (lit is the struct's first
+  // array), the code-length code's table lives in lsort meanwhile, and the
+  // lit/len code is built first: its sweep overwrites only lengths already
+  // read, and the distance lengths (index >= 257) lie in dist.
   __device__ void dynamic() {
+    static_assert((1 << kLaneLTB) + (1 << kLaneDTB) >= 286 + 30, "code lengths fit lit + dist");
+    static_assert(offsetof(LaneTables, dist) == sizeof(uint16_t) * (1 << kLaneLTB) * 32, "dist follows lit");
     uint16_t* lens = T->lit + lane;
     uint16_t* dtab = T->dist + lane;
+    uint16_t* ctab = T->lsort + lane;
     in.refill();
     if (in.avail() < 14) return finish(ST_TRUNCATED);
     const int nlen = (int)(in.bb & 31) + 257;
@@ -472,14 +489,14 @@ struct LaneDec {
     }
     for (int i = 0; i < 19; i++)
       lens[kClenOrder[i] * 32] = i < ncode ? (uint16_t)((cl >> (3 * i)) & 7) : 0;
-    if (lane_build<kLaneDTB>(lens, 19, 0, dtab, T->dsort + lane, T->dmeta + lane) != ST_OK)
+    if (lane_build<kLaneDTB>(lens, 19, 0, ctab, T->dsort + lane, T->dmeta + lane) != ST_OK)
       return finish(ST_BAD_HUFFMAN);
     const int total = nlen + ndist;
     int have = 0;
     while (have < total) {
       in.refill();
       const uint32_t avail = in.avail();
-      const uint32_t e = dtab[(uint32_t)(in.bb & 127) * 32];
+      const uint32_t e = ctab[(uint32_t)(in.bb & 127) * 32];
       const uint32_t L = e & 15;
       if (L > avail) return finish(ST_TRUNCATED);
       if ((e >> 13) != K_LIT) return finish(ST_BAD_HUFFMAN);
@@ -511,12 +528,12 @@ struct LaneDec {
       have += (int)rep;
     }
     if (lens[256 * 32] == 0) return finish(ST_BAD_HUFFMAN);
-    // distance code first: the lit/len table overwrites the code lengths
-    if (lane_build<kLaneDTB>(lens + nlen * 32, ndist, 2, dtab, T->dsort + lane, T->dmeta + lane) != ST_OK)
-      return finish(ST_BAD_HUFFMAN);
     if (lane_build<kLaneLTB>(lens, nlen, 1, T->lit + lane, T->lsort + lane, T->lmeta + lane) != ST_OK)
       return finish(ST_BAD_HUFFMAN);
+    if (lane_build<kLaneDTB>(lens + nlen * 32, ndist, 2, dtab, T->dsort + lane, T->dmeta + lane) != ST_OK)
+      return finish(ST_BAD_HUFFMAN);
     lt = T->lit + lane;
+    lm = (1u << kLaneLTB) - 1;
     dt = dtab;
     ls = ds = 32;
     state = LS_IN_BLOCK;
@@ -531,10 +548,10 @@ struct LaneDec {
   // next service phase decodes the same symbol again with step(), which makes
   // every check; nothing is consumed before that.
   __device__ __forceinline__ void fast_step() {
-    constexpr uint32_t LM = (1u << kLaneLTB) - 1, DM = (1u << kLaneDTB) - 1;
+    constexpr uint32_t DM = (1u << kLaneDTB) - 1;
     in.refill();
     const uint64_t bb = in.bb;
-    uint32_t e = lt[(uint32_t)(bb & LM) * ls];
+    uint32_t e = lt[((uint32_t)bb & lm) * ls];
     if ((e >> 13) == K_LONG) e = lane_long<kLaneLTB, 288>(bb, T->lmeta + lane, T->lsort + lane);
     const uint32_t k = e >> 13;
     const bool islit = k == K_LIT;
@@ -543,7 +560,7 @@ struct LaneDec {
     const uint32_t s1 = L + x;
     const uint64_t b1 = bb >> s1;
     const uint16_t* t2 = islit ? lt : dt;
-    uint32_t e2 = t2[((uint32_t)b1 & (islit ? LM : DM)) * (islit ? ls : ds)];
+    uint32_t e2 = t2[((uint32_t)b1 & (islit ? lm : DM)) * (islit ? ls : ds)];
     if (!islit && (e2 >> 13) == K_LONG) e2 = lane_long<kLaneDTB, 32>(b1, T->dmeta + lane, T->dsort + lane);
     const uint32_t k2 = e2 >> 13;
     const uint32_t L2 = e2 & 15;
@@ -578,10 +595,10 @@ struct LaneDec {
   // One symbol (state LS_IN_BLOCK), and a second one when both are table
   // literals.  The checks and their order are the serial decoder's.
   __device__ void step() {
-    constexpr uint32_t LM = (1u << kLaneLTB) - 1, DM = (1u << kLaneDTB) - 1;
+    constexpr uint32_t DM = (1u << kLaneDTB) - 1;
     in.refill();
     uint32_t avail = in.avail();
-    uint32_t e = lt[(uint32_t)(in.bb & LM) * ls];
+    uint32_t e = lt[((uint32_t)in.bb & lm) * ls];
     if ((e >> 13) == K_LONG) e = lane_long<kLaneLTB, 288>(in.bb, T->lmeta + lane, T->lsort + lane);
     const uint32_t L = e & 15;
     const uint32_t k = e >> 13;
@@ -598,7 +615,7 @@ struct LaneDec {
       in.consume(L);
       avail -= L;
       emit_literal((e >> 4) & 0xffu);
-      const uint32_t e2 = lt[(uint32_t)(in.bb & LM) * ls];
+      const uint32_t e2 = lt[((uint32_t)in.bb & lm) * ls];
       if ((e2 >> 13) == K_LIT && (e2 & 15) <= avail && (!STORE || wpos < cap)) {
         in.consume(e2 & 15);
         emit_literal((e2 >> 4) & 0xffu);
@@ -637,13 +654,13 @@ struct LaneDec {
 // 256-279, 8-bit codes 48-191 are 0-143, 8-bit codes 192-199 are 280-287,
 // 9-bit codes 400-511 are 144-255; distance codes are 5 bits.
 __device__ __forceinline__ void huf_cta_init(HufCta* F) {
-  for (uint32_t t = threadIdx.x; t < (1u << kLaneLTB); t += blockDim.x) {
+  for (uint32_t t = threadIdx.x; t < (1u << kFixLTB); t += blockDim.x) {
     uint32_t sym, L;
     if ((t >> 2) < 24) { sym = 256 + (t >> 2); L = 7; }
     else if ((t >> 1) < 192) { sym = (t >> 1) - 48; L = 8; }
     else if ((t >> 1) < 200) { sym = 280 + (t >> 1) - 192; L = 8; }
     else { sym = 144 + t - 400; L = 9; }
-    F->flit[__brev(t) >> (32 - kLaneLTB)] = (uint16_t)lane_sym_entry(1, L, sym);
+    F->flit[__brev(t) >> (32 - kFixLTB)] = (uint16_t)lane_sym_entry(1, L, sym);
   }
   for (uint32_t t = threadIdx.x; t < (1u << kLaneDTB); t += blockDim.x)
     F->fdist[__brev(t) >> (32 - kLaneDTB)] = (uint16_t)lane_sym_entry(2, 5, t >> 2);
