@@ -441,9 +441,12 @@ def main():
         total_ms = float(t.item())
         dist.barrier()
     value = job_bytes * args.steps / (total_ms / 1e3) / 1e9
-    kernel_ms = statistics.mean(ms)  # one decode launch per step (RLE)
+    # one decode launch per step for the RLE columns; the Deflate column's
+    # step is its two passes (Huffman, then LZ77) and the batch step the
+    # persistent kernel with its ordering and status kernels, timed together
+    kernel_ms = statistics.mean(ms)
     achieved = d.alg_bytes() / (kernel_ms / 1e3) / 1e9
-    kernel = {"rle_v1": "rle_v1_kernel", "rle_v2": "rle_v2_kernel", "deflate": "inflate_kernel",
+    kernel = {"rle_v1": "rle_v1_kernel", "rle_v2": "rle_v2_kernel", "deflate": "inflate_huffman_kernel",
               "batched": "batch_kernel", "byte_rle": "byte_rle_cta_kernel",
               "bool_rle": "byte_rle_cta_kernel", "orc_zlib": "orc_zlib_kernel"}[name]
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -451,6 +454,7 @@ def main():
                 "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                 "nominal_peak": NOMINAL_HBM_GBS,
                 "traffic": traffic_from_profile(kernel, w.n), "kernel": kernel,
+                "timed": "the whole step" if name in ("deflate", "batched") else "the kernel (one launch per step)",
                 "algorithmic_bytes_per_launch": d.alg_bytes()}
 
     # end to end through host buffers (pinned), copies inside the timed region
@@ -495,6 +499,11 @@ def main():
                    "parallelism": (f"chunk-parallel x{world} (one column split into balanced chunk ranges)"
                                    if args.split else f"chunk-parallel x{world} (independent columns per GPU)"),
                    "parts_per_chunk": codag.codag_get_parts_per_chunk() or "auto",
+                   **({"batch_ctas_per_sm": codag.codag_get_batch_ctas_per_sm() or "all that fit",
+                       "staging_depth": "%d x %d bytes per warp" % codag.codag_get_batch_staging(),
+                       "chunk_mapping": "RLE chunk of 2^b bytes on min(2^(b-%d), %d) warps"
+                                        % codag.codag_get_batch_split()}
+                      if name == "batched" else {}),
                    "tuning": tuned},
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s",
                 "h2d_bytes_per_step": w.comp_bytes + 16 * (w.n + 1),

@@ -284,6 +284,39 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm);
 int codag_get_batch_ctas_per_sm(void);
 
 /*
+ * Input staging of the batch kernel (CODAG Sec. IV-E: each decoder warp
+ * reads its chunk through a ring of input slots that the copy engine fills
+ * ahead of the decoder).  The batch kernel is compiled for a fixed set of
+ * ring shapes, SLOT bytes per slot x SLOTS slots per warp:
+ * 256 x 8, 512 x 8, 1024 x 4 (the default) and 2048 x 4.  A deeper ring keeps
+ * more input in flight per warp; a smaller one leaves room for more CTAs per
+ * SM.  codag_batch_staging_shapes writes up to `cap` shapes into the two
+ * arrays (either may be NULL) and returns how many are compiled.
+ * codag_set_batch_staging selects one (0, 0 = the default; any shape not
+ * compiled: CODAG_EINVAL, selection unchanged).  Takes effect for later calls
+ * and graph captures of the batch entry points, the no-alloc one included.
+ * Used by the autotuner; every shape decodes the same bytes.
+ */
+int codag_batch_staging_shapes(int *slot_bytes, int *slots, int cap);
+codag_status codag_set_batch_staging(int slot_bytes, int slots);
+codag_status codag_get_batch_staging(int *slot_bytes, int *slots);
+
+/*
+ * Chunk-to-warp mapping of the batch kernel for RLE chunks (CODAG Sec. IV-C:
+ * one warp per chunk, generalised to parts of one chunk).  A chunk whose
+ * compressed plus decoded size is 2^b to 2^(b+1) - 1 bytes is decoded by
+ * min(2^(b - split_log2), max_parts) warps when b > split_log2, else by one;
+ * each warp walks the run headers to its part's first value and decodes its
+ * part.  Deflate, byte RLE and ORC zlib chunks are always decoded whole.
+ * split_log2 in [8, 40], max_parts in [1, 32] (1: never split); (0, 0) = the
+ * default (16, 16); otherwise CODAG_EINVAL.  Takes effect for later calls and
+ * graph captures, the no-alloc entry point included.  Used by the autotuner;
+ * every mapping decodes the same bytes.
+ */
+codag_status codag_set_batch_split(int split_log2, int max_parts);
+codag_status codag_get_batch_split(int *split_log2, int *max_parts);
+
+/*
  * Warps per chunk for the plain RLE calls (codag_decompress with an RLE
  * format): one CTA per chunk runs this many warps.  A chunk staged whole in
  * shared memory is cut into segments of about 1024 values (256 for RLE v1):

@@ -78,6 +78,16 @@ def lib() -> ctypes.CDLL:
         L.codag_get_input_staging.restype = i32
         L.codag_set_deflate_pool_limit.argtypes = [u64]
         L.codag_get_deflate_pool_limit.restype = u64
+        ip = ctypes.POINTER(i32)
+        L.codag_batch_staging_shapes.argtypes = [ip, ip, i32]
+        L.codag_batch_staging_shapes.restype = i32
+        L.codag_set_batch_staging.argtypes = [i32, i32]
+        L.codag_get_batch_staging.argtypes = [ip, ip]
+        L.codag_set_batch_split.argtypes = [i32, i32]
+        L.codag_get_batch_split.argtypes = [ip, ip]
+        for name in ("codag_set_batch_staging", "codag_get_batch_staging",
+                     "codag_set_batch_split", "codag_get_batch_split"):
+            getattr(L, name).restype = i32
         L.codag_set_wait_limit_ns.argtypes = [u64]
         L.codag_get_wait_limit_ns.restype = u64
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
@@ -236,6 +246,34 @@ def codag_set_batch_ctas_per_sm(k: int):
 
 def codag_get_batch_ctas_per_sm() -> int:
     return lib().codag_get_batch_ctas_per_sm()
+
+
+def codag_batch_staging_shapes() -> list:
+    """Input-ring shapes the batch kernel is compiled for: [(slot_bytes, slots), ...]."""
+    n = lib().codag_batch_staging_shapes(None, None, 0)
+    a, b = (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)()
+    lib().codag_batch_staging_shapes(a, b, n)
+    return [(int(a[i]), int(b[i])) for i in range(n)]
+
+
+def codag_set_batch_staging(slot_bytes: int, slots: int):
+    _check(lib().codag_set_batch_staging(int(slot_bytes), int(slots)), "codag_set_batch_staging")
+
+
+def codag_get_batch_staging() -> tuple:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().codag_get_batch_staging(ctypes.byref(a), ctypes.byref(b)), "codag_get_batch_staging")
+    return int(a.value), int(b.value)
+
+
+def codag_set_batch_split(split_log2: int, max_parts: int):
+    _check(lib().codag_set_batch_split(int(split_log2), int(max_parts)), "codag_set_batch_split")
+
+
+def codag_get_batch_split() -> tuple:
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().codag_get_batch_split(ctypes.byref(a), ctypes.byref(b)), "codag_get_batch_split")
+    return int(a.value), int(b.value)
 
 
 def codag_set_parts_per_chunk(k: int):

@@ -18,6 +18,8 @@ namespace {
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_batch_ctas_per_sm{0};
+std::atomic<int> g_batch_shape{kBatchShapeDefault};  // index into batch_shape()
+std::atomic<uint32_t> g_split_lg{kSplitLgDefault}, g_split_max{kSplitMaxDefault};
 std::atomic<int> g_parts_per_chunk{0};
 std::atomic<int> g_reg_ring[8];  // per decoder family: 1 = register staging ring
 std::atomic<uint64_t> g_pool_limit{0};  // Deflate command pool bound in bytes (0: none)
@@ -112,7 +114,6 @@ codag_status current_ws(Workspace** out) {
                  {(const void*)byte_rle_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)byte_rle_sizes_kernel, kWarpsPerBlock * warp_chunk_smem(4, RleRing::SMEM)},
                  {(const void*)inflate_reg_kernel, kWarpsPerBlock * warp_chunk_smem(3, 0)},
-                 {(const void*)batch_kernel, kBatchSmem},
                  {(const void*)inflate_huffman_kernel, kHufSmem},
                  {(const void*)inflate_huffman_sizes_kernel, kHufSmem}};
     e = cudaDeviceGetAttribute(&w.sm_count, cudaDevAttrMultiProcessorCount, dev);
@@ -125,6 +126,11 @@ codag_status current_ws(Workspace** out) {
       // (rle_stage_bytes), up to the largest dynamic shared memory of a CTA
       const int bytes = at.bytes >= 0 ? at.bytes : w.smem_optin > kRleMaxSmem ? w.smem_optin : kRleMaxSmem;
       e = cudaFuncSetAttribute(at.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    }
+    for (int i = 0; i < kBatchShapes; i++) {
+      const BatchShape b = batch_shape(i);
+      e = cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b.smem);
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     }
     e = cudaMalloc(&w.counters, kBatchCounterWords * sizeof(uint32_t));
@@ -501,15 +507,21 @@ codag_status enqueue_batch(const Workspace& w, const uint8_t* formats, const voi
   a.order = order;
   a.counter = counters;
   a.keys = keys;
+  a.split_lg = g_split_lg.load();
+  a.split_max = g_split_max.load();
+  const BatchShape b = batch_shape(g_batch_shape.load());
   int fit = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, batch_kernel, kThreads, kBatchSmem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, b.fn, kThreads, b.smem);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
   int per_sm = g_batch_ctas_per_sm.load();
   if (per_sm <= 0 || per_sm > fit) per_sm = fit;
   if (per_sm < 1) per_sm = 1;
   const uint64_t grid = (uint64_t)per_sm * (uint64_t)w.sm_count;
-  batch_kernel<<<(unsigned)grid, kThreads, kBatchSmem, stream>>>(a);
-  batch_finalize_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n, keys, status);
+  void* params[] = {&a};
+  e = cudaLaunchKernel(b.fn, dim3((unsigned)grid), dim3(kThreads), params, (size_t)b.smem, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  batch_finalize_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n, keys, status,
+                                                a.split_lg, a.split_max);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   g_launches.fetch_add(4);
@@ -531,6 +543,7 @@ namespace codag {
 // For entry points defined in other translation units.
 void note_launches(uint64_t n) { g_launches.fetch_add(n); }
 void note_error(const std::string& msg) { g_last_error = msg; }
+int batch_shape_selected() { return g_batch_shape.load(); }
 }  // namespace codag
 
 struct codag_graph_s {
@@ -797,6 +810,61 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm) {
 
 int codag_get_batch_ctas_per_sm(void) { return g_batch_ctas_per_sm.load(); }
 
+int codag_batch_staging_shapes(int* slot_bytes, int* slots, int cap) {
+  for (int i = 0; i < kBatchShapes && i < cap; i++) {
+    const BatchShape b = batch_shape(i);
+    if (slot_bytes) slot_bytes[i] = b.slot;
+    if (slots) slots[i] = b.slots;
+  }
+  return kBatchShapes;
+}
+
+codag_status codag_set_batch_staging(int slot_bytes, int slots) {
+  if (slot_bytes == 0 && slots == 0) {
+    g_batch_shape.store(kBatchShapeDefault);
+    return CODAG_OK;
+  }
+  for (int i = 0; i < kBatchShapes; i++) {
+    const BatchShape b = batch_shape(i);
+    if (b.slot == slot_bytes && b.slots == slots) {
+      g_batch_shape.store(i);
+      return CODAG_OK;
+    }
+  }
+  return fail(CODAG_EINVAL, "codag_set_batch_staging: no batch kernel is compiled for a ring of " +
+                                std::to_string(slot_bytes) + " x " + std::to_string(slots) + " bytes");
+}
+
+codag_status codag_get_batch_staging(int* slot_bytes, int* slots) {
+  if (!slot_bytes || !slots) return fail(CODAG_EINVAL, "codag_get_batch_staging: NULL argument");
+  const BatchShape b = batch_shape(g_batch_shape.load());
+  *slot_bytes = b.slot;
+  *slots = b.slots;
+  return CODAG_OK;
+}
+
+codag_status codag_set_batch_split(int split_log2, int max_parts) {
+  if (split_log2 == 0 && max_parts == 0) {
+    g_split_lg.store(kSplitLgDefault);
+    g_split_max.store(kSplitMaxDefault);
+    return CODAG_OK;
+  }
+  if (split_log2 < 8 || split_log2 > 40)
+    return fail(CODAG_EINVAL, "codag_set_batch_split: split_log2 must be in [8, 40]");
+  if (max_parts < 1 || max_parts > (int)kSplitMaxLimit)
+    return fail(CODAG_EINVAL, "codag_set_batch_split: max_parts must be in [1, 32]");
+  g_split_lg.store((uint32_t)split_log2);
+  g_split_max.store((uint32_t)max_parts);
+  return CODAG_OK;
+}
+
+codag_status codag_get_batch_split(int* split_log2, int* max_parts) {
+  if (!split_log2 || !max_parts) return fail(CODAG_EINVAL, "codag_get_batch_split: NULL argument");
+  *split_log2 = (int)g_split_lg.load();
+  *max_parts = (int)g_split_max.load();
+  return CODAG_OK;
+}
+
 codag_status codag_set_parts_per_chunk(int parts) {
   if (parts < 0 || parts > 16) return fail(CODAG_EINVAL, "parts per chunk must be 0..16");
   g_parts_per_chunk.store(parts);
@@ -826,6 +894,8 @@ codag_status codag_set_wait_limit_ns(uint64_t ns) {
   cudaError_t e = set_wait_limit_rle(ns);
   if (e == cudaSuccess) e = set_wait_limit_inflate(ns);
   if (e == cudaSuccess) e = set_wait_limit_batch(ns);
+  if (e == cudaSuccess) e = set_wait_limit_batch_small(ns);
+  if (e == cudaSuccess) e = set_wait_limit_batch_large(ns);
   if (e != cudaSuccess) return cuda_fail(e, "wait limit");
   g_wait_limit.store(ns);
   return CODAG_OK;

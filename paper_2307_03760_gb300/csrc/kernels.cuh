@@ -62,8 +62,16 @@ constexpr int kRleMaxSmem = 16 * RleRing::SMEM + 16 * kRleScratch + kRleCtaExtra
 // 8 or 16 KiB window halves throughput (fewer CTAs fit), so none is used.
 constexpr int kBatchWin = 0;
 using BatchDeflateSmem = InflateSmem<kLitTB, kDistTB, kBatchWin>;
-constexpr int kBatchWarp =
-    round128(RleRing::SMEM + cmax(BatchDeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
+// RLE decoders ask their input ring for spans of up to 1,608 bytes (an RLE v2
+// run of 512 values of 25 bits, plus 8); every ring they read must cover that.
+constexpr int kRleMinSpan = 1664;
+static_assert(RleRing::MAX_SPAN >= kRleMinSpan, "RLE ring too shallow");
+// Per-warp shared memory of the batch kernel with input ring Ring: the ring
+// and the largest decoder scratch.
+template <class Ring>
+__host__ __device__ constexpr int batch_warp_bytes() {
+  return round128(Ring::SMEM + cmax(BatchDeflateSmem::BYTES, cmax(kRleV1Scratch, kRleV2Scratch)));
+}
 
 struct Args {
   const uint8_t* comp;
@@ -80,12 +88,15 @@ struct Args {
   unsigned long long* keys;  // batch kernel: combined status of multi-part chunks
   int stage_bytes;           // plain RLE kernels: shared staging area per CTA
   int deferred_only;         // one-warp Deflate kernel: decode only chunks whose status is kDeferred
+  uint32_t split_lg;         // batch kernel: RLE split rule (bucket_parts)
+  uint32_t split_max;
 };
 
 // Batch scratch: [0] task counter, [1..128] bucket histogram, [129..256]
 // bucket cursors.  Buckets order chunks largest first (2 * (63 - log2 of
 // compressed + uncompressed bytes) + 1 for Deflate); an RLE chunk of 2^b
-// bytes is split into clamp(2^(b-16), 1, 16) parts.
+// bytes is split into min(2^(b - split_lg), split_max) parts when b >
+// split_lg, else decoded whole (the default rule: split_lg 16, split_max 16).
 constexpr int kBuckets = 128;
 constexpr int kBatchCounterWords = 1 + 2 * kBuckets;
 
@@ -100,11 +111,16 @@ __device__ __forceinline__ uint32_t batch_bucket(const uint8_t* formats, const u
   return 2u * (63u - lg) + (is_rle_format(formats[c]) ? 0u : 1u);
 }
 
-__host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket) {
+constexpr uint32_t kSplitLgDefault = 16, kSplitMaxDefault = 16, kSplitMaxLimit = 32;
+
+__host__ __device__ __forceinline__ uint32_t bucket_parts(uint32_t bucket, uint32_t split_lg,
+                                                          uint32_t split_max) {
   if (bucket & 1u) return 1u;
-  const int lg = 63 - (int)(bucket >> 1);
-  if (lg <= 16) return 1u;
-  return lg >= 20 ? 16u : (1u << (lg - 16));
+  const uint32_t lg = 63u - (bucket >> 1);
+  if (lg <= split_lg) return 1u;
+  const uint32_t d = lg - split_lg;
+  const uint32_t p = d >= 6 ? 64u : (1u << d);
+  return p < split_max ? p : split_max;
 }
 
 // Plain kernels.  RLE: one CTA per chunk, blockDim.x / 32 warps decoding its
@@ -134,8 +150,23 @@ __global__ void inflate_huffman_kernel(Args a, HufArgs h);
 __global__ void inflate_huffman_sizes_kernel(Args a, HufArgs h);
 __global__ void inflate_lz77_kernel(Args a, HufArgs h);
 
-// Persistent batch kernel: warps claim (chunk, part) tasks in bucket order.
-__global__ void batch_kernel(Args a);
+// Persistent batch kernel (batch.cuh): warps claim (chunk, part) tasks in
+// bucket order, each warp reading its input through a shared-memory ring of
+// SLOT x SLOTS bytes.  It is compiled for kBatchShapes ring shapes and one is
+// chosen at launch (codag_set_batch_staging).
+struct BatchShape {
+  int slot;        // bytes per ring slot
+  int slots;       // slots per ring
+  const void* fn;  // the kernel instance
+  int smem;        // its dynamic shared memory per CTA
+};
+constexpr int kBatchShapes = 4;
+constexpr int kBatchShapeDefault = 2;  // 1024 x 4
+BatchShape batch_shape(int i);  // i in [0, kBatchShapes): 256x8, 512x8, 1024x4, 2048x4
+BatchShape batch_shape_256x8();
+BatchShape batch_shape_512x8();
+BatchShape batch_shape_1024x4();
+BatchShape batch_shape_2048x4();
 
 // claim order for the batch kernel (counting sort by bucket)
 __global__ void order_hist_kernel(const uint8_t* formats, const uint64_t* comp_off,
@@ -146,15 +177,22 @@ __global__ void order_scatter_kernel(const uint8_t* formats, const uint64_t* com
 // status of multi-part chunks from their combined keys
 __global__ void batch_finalize_kernel(const uint8_t* formats, const uint64_t* comp_off,
                                       const uint64_t* out_off, uint64_t n,
-                                      const unsigned long long* keys, int32_t* status);
+                                      const unsigned long long* keys, int32_t* status,
+                                      uint32_t split_lg, uint32_t split_max);
 
 // Host: set the work-wait bound (codag_set_wait_limit_ns) in each unit that
 // has bounded device waits.
 cudaError_t set_wait_limit_rle(uint64_t ns);
 cudaError_t set_wait_limit_inflate(uint64_t ns);
 cudaError_t set_wait_limit_batch(uint64_t ns);
+cudaError_t set_wait_limit_batch_small(uint64_t ns);
+cudaError_t set_wait_limit_batch_large(uint64_t ns);
 
-// Dynamic shared memory of the batch kernel: per-warp regions + bucket tables.
-constexpr int kBatchSmem = kWarpsPerBlock * kBatchWarp + 2 * (kBuckets + 1) * 4;
+// Dynamic shared memory of the batch kernel with input ring Ring: per-warp
+// regions + bucket tables.
+template <class Ring>
+__host__ __device__ constexpr int batch_smem() {
+  return kWarpsPerBlock * batch_warp_bytes<Ring>() + 2 * (kBuckets + 1) * 4;
+}
 
 }  // namespace codag

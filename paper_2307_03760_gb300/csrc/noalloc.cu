@@ -14,8 +14,8 @@
 // the process exits.  Host code may not use the array's name as a device
 // address; the first call on each device, with that device current, asks the
 // runtime for the array's address with cudaGetSymbolAddress and keeps it.
-// That first call also sets the kernel's shared-memory attribute, so make it
-// before any stream capture.
+// That first call also sets the shared-memory attribute of every compiled
+// shape of the batch kernel, so make it before any stream capture.
 //
 // All calls on a device share the one array and it keeps the last call's
 // contents: each call clears the parts that must start at zero (or all ones)
@@ -30,6 +30,7 @@
 namespace codag {
 void note_launches(uint64_t n);
 void note_error(const std::string& msg);
+int batch_shape_selected();
 }  // namespace codag
 
 using namespace codag;
@@ -49,7 +50,7 @@ struct DeviceSetup {
   bool ready = false;
   uint8_t* scratch = nullptr;  // device address of g_noalloc_scratch
   int sm_count = 0;
-  int fit = 0;  // resident batch CTAs per SM
+  int fit[kBatchShapes] = {};  // resident batch CTAs per SM, per ring shape
 };
 
 constexpr int kMaxDevices = 64;
@@ -74,16 +75,18 @@ codag_status setup_current_device(DeviceSetup** out) {
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess)
       return fail(CODAG_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    const size_t smem = kBatchSmem;
-    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess)
-      return fail(CODAG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     e = cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
       return fail(CODAG_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.fit, batch_kernel, kThreads, smem);
-    if (e != cudaSuccess)
-      return fail(CODAG_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    for (int i = 0; i < kBatchShapes; i++) {
+      const BatchShape b = batch_shape(i);
+      e = cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b.smem);
+      if (e != cudaSuccess)
+        return fail(CODAG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.fit[i], b.fn, kThreads, b.smem);
+      if (e != cudaSuccess)
+        return fail(CODAG_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+    }
     s.scratch = static_cast<uint8_t*>(p);
     s.ready = true;
   }
@@ -133,13 +136,21 @@ extern "C" codag_status codag_decompress_batch_noalloc(const uint8_t* formats, c
   a.order = order;
   a.counter = counters;
   a.keys = keys;
+  int split_lg = 0, split_max = 0;
+  codag_get_batch_split(&split_lg, &split_max);
+  a.split_lg = (uint32_t)split_lg;
+  a.split_max = (uint32_t)split_max;
+  const int shape = batch_shape_selected();
+  const BatchShape b = batch_shape(shape);
   int per_sm = codag_get_batch_ctas_per_sm();
-  if (per_sm <= 0 || per_sm > s->fit) per_sm = s->fit;
+  if (per_sm <= 0 || per_sm > s->fit[shape]) per_sm = s->fit[shape];
   if (per_sm < 1) per_sm = 1;
   const uint64_t grid = (uint64_t)per_sm * (uint64_t)s->sm_count;
-  batch_kernel<<<(unsigned)grid, kThreads, kBatchSmem, stream>>>(a);
+  void* params[] = {&a};
+  e = cudaLaunchKernel(b.fn, dim3((unsigned)grid), dim3(kThreads), params, (size_t)b.smem, stream);
+  if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   batch_finalize_kernel<<<og, 256, 0, stream>>>(formats, comp_offsets, out_offsets, n_chunks, keys,
-                                                chunk_status);
+                                                chunk_status, a.split_lg, a.split_max);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CODAG_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   note_launches(4);

@@ -95,6 +95,50 @@ def test_input_staging_setting():
         assert L.codag_get_input_staging(f) == 0
 
 
+def test_batch_staging_selection():
+    """The batch kernel's compiled ring shapes are listed, each can be
+    selected, anything else is refused and leaves the selection alone."""
+    shapes = codag.codag_batch_staging_shapes()
+    assert shapes == [(256, 8), (512, 8), (1024, 4), (2048, 4)]
+    assert codag.codag_get_batch_staging() == (1024, 4)  # default
+    L = codag.lib()
+    try:
+        for shape in shapes:
+            codag.codag_set_batch_staging(*shape)
+            assert codag.codag_get_batch_staging() == shape
+        codag.codag_set_batch_staging(512, 8)
+        for bad in ((512, 4), (1024, 3), (4096, 4), (-1, 4), (0, 4)):
+            assert L.codag_set_batch_staging(*bad) == codag.CODAG_EINVAL
+            assert codag.codag_get_batch_staging() == (512, 8)
+        assert b"no batch kernel is compiled" in L.codag_last_error()
+        # a short array takes only the first shapes; the count is still returned
+        a = (ctypes.c_int32 * 2)()
+        assert L.codag_batch_staging_shapes(a, None, 2) == len(shapes)
+        assert list(a) == [256, 512]
+        codag.codag_set_batch_staging(0, 0)
+        assert codag.codag_get_batch_staging() == (1024, 4)
+    finally:
+        codag.codag_set_batch_staging(0, 0)
+
+
+def test_batch_split_selection():
+    assert codag.codag_get_batch_split() == (16, 16)  # default
+    L = codag.lib()
+    try:
+        codag.codag_set_batch_split(12, 32)
+        assert codag.codag_get_batch_split() == (12, 32)
+        codag.codag_set_batch_split(20, 1)
+        assert codag.codag_get_batch_split() == (20, 1)
+        for bad in ((7, 4), (41, 4), (16, 0), (16, 33), (0, 4), (16, -1)):
+            assert L.codag_set_batch_split(*bad) == codag.CODAG_EINVAL
+            assert codag.codag_get_batch_split() == (20, 1)
+        assert L.codag_get_batch_split(None, None) == codag.CODAG_EINVAL
+        codag.codag_set_batch_split(0, 0)
+        assert codag.codag_get_batch_split() == (16, 16)
+    finally:
+        codag.codag_set_batch_split(0, 0)
+
+
 def test_deflate_pool_limit_setting():
     assert codag.codag_get_deflate_pool_limit() == 0  # default: no bound
     codag.codag_set_deflate_pool_limit(1 << 20)

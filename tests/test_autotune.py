@@ -31,17 +31,74 @@ def test_apply_loads_every_knob(tmp_path):
     import paper_2307_03760_gb300 as codag
     from paper_2307_03760_gb300 import autotune
     table = {"batch_ctas_per_sm": {"best": 2}, "rle_parts": {"rle_v2": {"chunks": 10, "best": 8}},
-             "input_staging": {"deflate": {"format": 3, "best": 1}, "byte_rle": {"format": 6, "best": 1}}}
+             "input_staging": {"deflate": {"format": 3, "best": 1}, "byte_rle": {"format": 6, "best": 1}},
+             "staging_depth": {"best": [2048, 4]}, "chunk_mapping": {"best": [14, 32]}}
     p = tmp_path / "t.json"
     p.write_text(json.dumps(table))
     try:
         done = autotune.apply(str(p), n_chunks=10, family="rle_v2")
         assert done["batch_ctas_per_sm"] == 2 and done["parts_per_chunk"] == 8
+        assert done["staging_depth"] == [2048, 4] and codag.codag_get_batch_staging() == (2048, 4)
+        assert done["chunk_mapping"] == [14, 32] and codag.codag_get_batch_split() == (14, 32)
         assert codag.codag_get_input_staging(3) == 1 and codag.codag_get_input_staging(7) == 1
         done = autotune.apply(str(p), n_chunks=11, family="rle_v2")
         assert "parts_per_chunk" not in done
     finally:
         codag.codag_set_batch_ctas_per_sm(0)
+        codag.codag_set_batch_staging(0, 0)
+        codag.codag_set_batch_split(0, 0)
         codag.codag_set_parts_per_chunk(0)
         for f in (3, 6, 7):
             codag.codag_set_input_staging(f, 0)
+
+
+def test_joint_batch_selection_over_shape_and_ctas():
+    """The batch sweep's candidates are (slot, slots, ctas) triples; the
+    fastest median wins and a near-tie goes to the smaller ring."""
+    import paper_2307_03760_gb300 as codag
+    from paper_2307_03760_gb300 import autotune
+    shapes = codag.codag_batch_staging_shapes()
+    cands = [(a, b, k) for a, b in shapes for k in autotune.BATCH_CTAS]
+    fake = {c: 10.0 + abs(c[2] - 4) + (0.5 if c[0] == 1024 else 1.0) for c in cands}
+    state = {}
+    t = autotune.sweep(lambda: None, cands, lambda c: state.update(c=c), reps=3, warmup=0,
+                       timer=lambda fn: fake[state["c"]])
+    assert autotune.choose(t)[0] == (1024, 4, 4)
+    fake[(512, 8, 4)] = fake[(1024, 4, 4)]
+    t = autotune.sweep(lambda: None, cands, lambda c: state.update(c=c), reps=3, warmup=0,
+                       timer=lambda fn: fake[state["c"]])
+    assert autotune.choose(t)[0] == (512, 8, 4)
+    assert autotune._key((1024, 4, 4)) == "1024x4x4"
+
+
+def test_split_rules_offered_are_accepted():
+    """Every split rule the sweep offers is one the library takes."""
+    import paper_2307_03760_gb300 as codag
+    from paper_2307_03760_gb300 import autotune
+    assert (16, 16) in autotune.SPLIT_RULES and (16, 1) in autotune.SPLIT_RULES
+    try:
+        for r in autotune.SPLIT_RULES:
+            codag.codag_set_batch_split(*r)
+            assert codag.codag_get_batch_split() == r
+    finally:
+        codag.codag_set_batch_split(0, 0)
+
+
+def test_committed_table_entries_are_valid():
+    """The committed GB300 table names a compiled ring shape and a valid
+    split rule, and records the sweeps they came from."""
+    import json
+    import os
+
+    import paper_2307_03760_gb300 as codag
+    from paper_2307_03760_gb300 import autotune
+    if not os.path.exists(autotune.DEFAULT_TABLE):
+        return
+    table = json.load(open(autotune.DEFAULT_TABLE))
+    if "staging_depth" not in table:
+        return
+    assert tuple(table["staging_depth"]["best"]) in codag.codag_batch_staging_shapes()
+    assert tuple(table["chunk_mapping"]["best"]) in autotune.SPLIT_RULES
+    assert len(table["sweeps"]["batch_staging_x_ctas"]) == \
+        len(codag.codag_batch_staging_shapes()) * len(autotune.BATCH_CTAS)
+    assert len(table["sweeps"]["batch_split"]) == len(autotune.SPLIT_RULES)

@@ -233,6 +233,52 @@ def test_batch_mixed_and_graph():
     assert (st2 == 0).all() and np.array_equal(got2, w.plain)
 
 
+SPLITS = [(16, 16), (12, 32), (14, 4), (16, 1)]
+
+
+@pytest.mark.parametrize("split", SPLITS, ids=lambda s: f"split{s[0]}max{s[1]}")
+def test_batch_every_staging_shape_and_split(split):
+    """Every compiled input-ring shape of the batch kernel, under several RLE
+    split rules (fine, coarse, never), decodes every chunk to the same bytes;
+    also through a graph captured with the non-default choices."""
+    shapes = codag.codag_batch_staging_shapes()
+    assert len(shapes) >= 4 and (1024, 4) in shapes
+    w = synth.batched(seed=5, n_chunks=300, lo=512, hi=1 << 20, keep_plain=True)
+    try:
+        codag.codag_set_batch_split(*split)
+        for slot, slots in shapes:
+            codag.codag_set_batch_staging(slot, slots)
+            got, st = run_batch(w.formats, w.comp, w.comp_off, w.out_off)
+            assert (st == 0).all(), (slot, slots)
+            assert np.array_equal(got, w.plain), (slot, slots)
+        got, st = run_batch(w.formats, w.comp, w.comp_off, w.out_off, graph=True, replays=2)
+        assert (st == 0).all() and np.array_equal(got, w.plain)
+    finally:
+        codag.codag_set_batch_staging(0, 0)
+        codag.codag_set_batch_split(0, 0)
+
+
+@pytest.mark.parametrize("shape", [(256, 8), (2048, 4)])
+def test_batch_errors_non_default_shape(shape):
+    """Corrupted and truncated chunks give the oracle's statuses with a
+    non-default ring shape and fine RLE splitting (errors inside parts)."""
+    w = synth.batched(seed=8, n_chunks=96, lo=512, hi=1 << 20)
+    comp = w.comp.copy()
+    rng = np.random.default_rng(9)
+    for c in range(1, w.n, 4):
+        a, b = int(w.comp_off[c]), int(w.comp_off[c + 1])
+        if b > a:
+            comp[rng.integers(a, b)] ^= 0x33
+    try:
+        codag.codag_set_batch_staging(*shape)
+        codag.codag_set_batch_split(12, 32)
+        got, st = run_batch(w.formats, comp, w.comp_off, w.out_off)
+    finally:
+        codag.codag_set_batch_staging(0, 0)
+        codag.codag_set_batch_split(0, 0)
+    assert_parity(0, comp, w.comp_off, w.out_off, got, st, formats=w.formats)
+
+
 def test_batch_unknown_format_and_errors():
     w = synth.batched(seed=4, n_chunks=64, lo=512, hi=1 << 20)
     fm = w.formats.copy()

@@ -59,6 +59,21 @@ def test_noalloc_matches_batch_two_calls_in_a_row():
         assert np.array_equal(out, w.plain)
 
 
+def test_noalloc_follows_staging_and_split_choice():
+    """The no-alloc entry point launches the selected ring shape and split rule."""
+    w = synth.batched(seed=21, n_chunks=400, lo=512, hi=1 << 19, keep_plain=True)
+    try:
+        for shape, split in (((256, 8), (12, 32)), ((2048, 4), (16, 1))):
+            codag.codag_set_batch_staging(*shape)
+            codag.codag_set_batch_split(*split)
+            out, st = _noalloc(w)
+            assert (st == 0).all(), shape
+            assert np.array_equal(out, w.plain), shape
+    finally:
+        codag.codag_set_batch_staging(0, 0)
+        codag.codag_set_batch_split(0, 0)
+
+
 def test_noalloc_rejects_too_many_chunks():
     n = codag.CODAG_NOALLOC_MAX_CHUNKS + 1
     dummy = torch.zeros(64, dtype=torch.uint8, device=DEV)
