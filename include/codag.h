@@ -284,6 +284,22 @@ codag_status codag_set_batch_ctas_per_sm(int ctas_per_sm);
 int codag_get_batch_ctas_per_sm(void);
 
 /*
+ * Header walk of the plain RLE v2 calls (codag_decompress and
+ * codag_decompress_host with an RLE v2 format; CODAG Sec. II-B: decoders
+ * start independently where the stream's boundaries are known).  A chunk staged whole is cut into segments of
+ * about 1024 values that start at run boundaries, found by walking its run
+ * headers.  mode 0 (the default): each chunk's CTA walks its own chunk while
+ * its other warps decode the segments already found.  mode 1: a walk pass,
+ * one warp per chunk, walks every chunk at once and writes the segment
+ * starts (512 bytes of library workspace per chunk, calls of up to 2^18
+ * chunks); the decode pass then decodes segments with no wait.  Other
+ * formats: CODAG_EINVAL (get: -1).  Takes effect for later calls; both modes
+ * decode the same bytes.  Used by the autotuner.
+ */
+codag_status codag_set_walk_pass(int format, int mode);
+int codag_get_walk_pass(int format);
+
+/*
  * Input staging of the batch kernel (CODAG Sec. IV-E: each decoder warp
  * reads its chunk through a ring of input slots that the copy engine fills
  * ahead of the decoder).  The batch kernel is compiled for a fixed set of

@@ -88,6 +88,10 @@ def lib() -> ctypes.CDLL:
         for name in ("codag_set_batch_staging", "codag_get_batch_staging",
                      "codag_set_batch_split", "codag_get_batch_split"):
             getattr(L, name).restype = i32
+        L.codag_set_walk_pass.argtypes = [i32, i32]
+        L.codag_set_walk_pass.restype = i32
+        L.codag_get_walk_pass.argtypes = [i32]
+        L.codag_get_walk_pass.restype = i32
         L.codag_set_wait_limit_ns.argtypes = [u64]
         L.codag_get_wait_limit_ns.restype = u64
         for name in ("codag_decompress", "codag_decompressed_sizes", "codag_decompress_batch",
@@ -246,6 +250,14 @@ def codag_set_batch_ctas_per_sm(k: int):
 
 def codag_get_batch_ctas_per_sm() -> int:
     return lib().codag_get_batch_ctas_per_sm()
+
+
+def codag_set_walk_pass(fmt, mode: int):
+    _check(lib().codag_set_walk_pass(_fmt(fmt), int(mode)), "codag_set_walk_pass")
+
+
+def codag_get_walk_pass(fmt) -> int:
+    return lib().codag_get_walk_pass(_fmt(fmt))
 
 
 def codag_batch_staging_shapes() -> list:

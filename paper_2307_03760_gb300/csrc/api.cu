@@ -18,6 +18,13 @@ namespace {
 thread_local std::string g_last_error;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_batch_ctas_per_sm{0};
+// plain RLE v2: walk pass before the decode pass (1) or the walk inside each
+// decode CTA (0, the default: faster on GB300 for the 128 KiB-chunk column,
+// 104 against 127 us); codag_set_walk_pass
+std::atomic<int> g_walk_pass{0};
+// the walk pass's table is kMaxSeg * 8 bytes per chunk: calls with more
+// chunks than this walk inside the decode CTAs
+constexpr uint64_t kMaxWalkChunks = 1ull << 18;
 std::atomic<int> g_batch_shape{kBatchShapeDefault};  // index into batch_shape()
 std::atomic<uint32_t> g_split_lg{kSplitLgDefault}, g_split_max{kSplitMaxDefault};
 std::atomic<int> g_parts_per_chunk{0};
@@ -87,6 +94,9 @@ struct Workspace {
   uint32_t* hctr = nullptr;
   unsigned long long* hneed = nullptr;
   unsigned long long* hneed_host = nullptr;
+  // RLE v2 walk pass: kMaxSeg segment-start entries per chunk
+  uint2* seg = nullptr;
+  uint64_t seg_cap = 0;  // chunks
 };
 
 std::mutex g_mu;
@@ -166,6 +176,25 @@ codag_status grow_order(Workspace& w, uint64_t n) {
     return fail(CODAG_ENOMEM, "order workspace allocation failed");
   w.order_cap = cap;
   return CODAG_OK;
+}
+
+// The walk pass's segment table for n chunks, or nullptr when the call walks
+// inside its decode CTAs (not RLE v2, the walk pass switched off, too many
+// chunks, or no memory for the table).
+uint2* walk_table(Workspace& w, int fam, uint64_t n, bool store) {
+  if (fam != 2 || !store || g_walk_pass.load() != 1 || n > kMaxWalkChunks) return nullptr;
+  if (n > w.seg_cap) {
+    if (w.seg) cudaFree(w.seg);
+    w.seg = nullptr;
+    w.seg_cap = 0;
+    const uint64_t cap = n < 1024 ? 1024 : (n + n / 4 < kMaxWalkChunks ? n + n / 4 : kMaxWalkChunks);
+    if (cudaMalloc(&w.seg, cap * kMaxSeg * sizeof(uint2)) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    w.seg_cap = cap;
+  }
+  return w.seg;
 }
 
 bool is_rle(int f) {
@@ -264,7 +293,8 @@ DeflateRun deflate_run(const Workspace& w, uint64_t region, uint64_t first, int 
 codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
                            const uint64_t* comp_offsets, uint64_t n, void* out,
                            const uint64_t* out_offsets, uint64_t* sizes, bool store,
-                           int32_t* status, cudaStream_t stream, const DeflateRun* dr = nullptr);
+                           int32_t* status, cudaStream_t stream, const DeflateRun* dr = nullptr,
+                           uint2* seg = nullptr);
 
 codag_status launch_plain(int format, const void* comp, const uint64_t* comp_offsets, uint64_t n,
                           void* out, const uint64_t* out_offsets, uint64_t* sizes, bool store,
@@ -299,7 +329,7 @@ codag_status launch_plain(int format, const void* comp, const uint64_t* comp_off
     return s;
   }
   return launch_kernel(*w, format, comp, comp_offsets, n, out, out_offsets, sizes, store, w->status,
-                       stream);
+                       stream, nullptr, walk_table(*w, fam, n, store));
 }
 
 // Whole-chunk stage of a CTA-per-chunk RLE launch (family fam, `parts`
@@ -343,7 +373,8 @@ int rle_stage_bytes(const Workspace& w, const void* fn, int fam, int parts, bool
 codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
                            const uint64_t* comp_offsets, uint64_t n, void* out,
                            const uint64_t* out_offsets, uint64_t* sizes, bool store,
-                           int32_t* status, cudaStream_t stream, const DeflateRun* dr) {
+                           int32_t* status, cudaStream_t stream, const DeflateRun* dr,
+                           uint2* seg) {
   const Workspace* w = &ws;
   const int fam = family_of(format);
   Args a{};
@@ -417,6 +448,16 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     a.stage_bytes = stage;
     smem = (size_t)stage + (size_t)parts * kRleScratch + kRleCtaExtra;
     if (fam == 1) smem += (size_t)rle_v1_bitmap_bytes(stage);
+    if (fam == 2 && store && seg && parts > 1) {
+      // walk pass: every chunk's segment starts, before the decode pass
+      a.seg = seg;
+      a.parts = parts;
+      rle_v2_walk_kernel<<<(unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock), kThreads,
+                           kWarpsPerBlock * RleRing::SMEM, stream>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "walk launch");
+      g_launches.fetch_add(1);
+    }
   }
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(block), params, smem, stream);
@@ -603,6 +644,7 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
   const uint64_t per_sm = fam == 3 ? 32 * kHufWarps : fam >= 4 ? 40 : 8;
   const uint64_t min_chunks = (uint64_t)w->sm_count * per_sm / kPipeDecode;
   const std::vector<uint64_t> bounds = plan_slices(h_out_offsets, n, min_chunks);
+  uint2* seg = walk_table(*w, fam, n, true);
   uint64_t* d_coff = p.offs;
   uint64_t* d_ooff = p.offs + (n + 1);
   const uint8_t* hc = static_cast<const uint8_t*>(h_comp);
@@ -637,7 +679,8 @@ codag_status codag_decompress_host(int format, const void* h_comp, const uint64_
     if (e != cudaSuccess) return cuda_fail(e, "codag_decompress_host copy in");
     const DeflateRun dr = deflate_run(*w, (h_out_offsets[a] - h_out_offsets[0]) / 4 + 2 * a, a, (int)k);
     s = launch_kernel(*w, format, d_comp, d_coff + a, b - a, d_out, d_ooff + a, nullptr, true,
-                      w->status + a, ds, family_of(format) == 3 ? &dr : nullptr);
+                      w->status + a, ds, family_of(format) == 3 ? &dr : nullptr,
+                      seg ? seg + a * kMaxSeg : nullptr);
     if (s != CODAG_OK) return s;
     e = cudaEventRecord(p.decoded[k], ds);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p.d2h, p.decoded[k], 0);
@@ -842,6 +885,15 @@ codag_status codag_get_batch_staging(int* slot_bytes, int* slots) {
   *slots = b.slots;
   return CODAG_OK;
 }
+
+codag_status codag_set_walk_pass(int format, int mode) {
+  if (family_of(format) != 2) return fail(CODAG_EINVAL, "codag_set_walk_pass: RLE v2 formats only");
+  if (mode != 0 && mode != 1) return fail(CODAG_EINVAL, "codag_set_walk_pass: mode must be 0 or 1");
+  g_walk_pass.store(mode);
+  return CODAG_OK;
+}
+
+int codag_get_walk_pass(int format) { return family_of(format) == 2 ? g_walk_pass.load() : -1; }
 
 codag_status codag_set_batch_split(int split_log2, int max_parts) {
   if (split_log2 == 0 && max_parts == 0) {

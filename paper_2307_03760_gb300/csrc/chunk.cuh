@@ -54,6 +54,15 @@ __device__ __forceinline__ uint64_t part_target(uint64_t cap_v, uint32_t k, uint
   return q * k + (k < rem ? k : rem);
 }
 
+// Segments of a chunk staged whole by the plain RLE kernels (K warps): about
+// kSegValues values each (kSegValuesV1 for RLE v1, kSegBytesByteRle decoded
+// bytes for byte RLE), at least K, at most kMaxSeg.
+template <int FAMILY>
+__host__ __device__ __forceinline__ uint32_t rle_seg_count(uint64_t cap_v, uint32_t K) {
+  const uint64_t want = cap_v / (FAMILY == 1 ? kSegValuesV1 : FAMILY == 4 ? kSegBytesByteRle : kSegValues);
+  return want < K ? K : want > (uint64_t)kMaxSeg ? (uint32_t)kMaxSeg : (uint32_t)want;
+}
+
 // Decode one part: the sub-stream of `in` starting at byte `base` (a run or
 // group boundary whose first value index is count0), through the runs that
 // start before value hi.  Error positions come back chunk-relative.
@@ -197,14 +206,19 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   // boolean RLE)
   const uint64_t cap_v = FAMILY != 4 ? g.cap / 8 : a.format == FMT_BOOL_RLE ? (g.cap + 7) / 8 : g.cap;
   // segments: about kSegValues values each, at least K, at most kMaxSeg
-  uint32_t nseg = K;
-  if (staged && STORE) {
-    const uint64_t want = cap_v / (FAMILY == 1 ? kSegValuesV1 : FAMILY == 4 ? kSegBytesByteRle : kSegValues);
-    nseg = want < K ? K : want > (uint64_t)kMaxSeg ? (uint32_t)kMaxSeg : (uint32_t)want;
-  }
+  const uint32_t nseg = (staged && STORE) ? rle_seg_count<FAMILY>(cap_v, K) : K;
+  // RLE v2 segment starts written by the walk pass (rle_v2_walk_kernel)
+  const uint2* segt = (FAMILY == 2 && STORE && staged && nseg > 1 && a.seg) ? a.seg + c * kMaxSeg : nullptr;
+  const bool prewalked = segt && segt[0].x == 1u;
+  if (prewalked)
+    for (uint32_t t = 1 + threadIdx.x; t < nseg; t += blockDim.x) {
+      const uint2 e = segt[t];
+      split_pos[t] = e.x;
+      split_cnt[t] = e.y;
+    }
   if (threadIdx.x == 0) {
     *key = ~0ull;
-    *published = 1;
+    *published = prewalked ? nseg : 1;
     *claimed = 0;
     split_pos[0] = 0;
     split_cnt[0] = 0;
@@ -260,7 +274,7 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
     if (!ok) {
       if (threadIdx.x == 0) *key = status_key(PartResult{ST_TIMEOUT, 0, 0});
     } else {
-      if (warp == 0 && nseg > 1) {
+      if (warp == 0 && nseg > 1 && !prewalked) {
         if (FAMILY == 1 && nx_off)
           rle_v1_walk_next(reinterpret_cast<const uint32_t*>(stage + nx_off), (uint32_t)g.n_in,
                            target, (int)nseg - 1, split_pos, split_cnt, published);
@@ -327,6 +341,60 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
   }
   __syncthreads();
   if (threadIdx.x == 0) a.status[c] = key_status(*key);
+}
+
+// Walk pass of the plain RLE v2 call (one warp per chunk): for every chunk
+// that the decode pass (a.parts warps per CTA, a.stage_bytes of stage) stages
+// whole and cuts into nseg > 1 segments, walk its run headers through a TMA
+// ring and write where each segment starts, as rle_v2_walk_staged would
+// publish it.  Every chunk's walk runs at once here, instead of one walk at a
+// time on the critical path of each decode CTA.  A chunk that the walk pass
+// leaves (other geometry, a value count past 32 bits, a wait that ran out)
+// gets flag 0, and its decode CTA walks it itself.
+__device__ __forceinline__ void rle_v2_walk_body(const Args& a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint64_t c = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (c >= a.n) return;
+  RleRing ring;
+  ring.init(smem + warp * RleRing::SMEM);
+  uint2* segt = a.seg + c * kMaxSeg;
+  const ChunkGeom g = chunk_geom<2, true>(a, c);
+  const uint64_t cap_v = g.cap / 8;
+  const uint32_t nseg = rle_seg_count<2>(cap_v, (uint32_t)a.parts);
+  if (g.bad != ST_OK || staged_bytes(g.n_in) > a.stage_bytes || nseg <= 1 || cap_v >= (1ull << 32)) {
+    if (lane_id() == 0) segt[0] = make_uint2(0u, 0u);
+    return;
+  }
+  const uint32_t n_in = (uint32_t)g.n_in;
+  const uint32_t q = (uint32_t)(cap_v / nseg), rem = (uint32_t)(cap_v % nseg);
+  ring.start(a.comp + g.cs, g.n_in, a.comp + a.comp_off[a.n]);
+  uint32_t pos = 0, count = 0, k = 1;
+  uint32_t tk = q + (1 < rem ? 1 : rem);  // part_target(cap_v, 1, nseg)
+  bool ok = true;
+  while (pos < n_in) {
+    if (count >= tk) {
+      do {
+        if (lane_id() == 0) segt[k] = make_uint2(pos, count);
+        if (++k >= nseg) break;
+        tk = q * k + (k < rem ? k : rem);
+      } while (count >= tk);
+      if (k >= nseg) break;
+    }
+    if (!ring.ensure(pos, pos + 40)) {
+      ok = false;
+      break;
+    }
+    uint32_t len, end;
+    if (!v2_run_extent(ring, pos, n_in, &len, &end)) break;
+    count += len;
+    pos = end;
+  }
+  if (ok)
+    for (; k < nseg; k++)
+      if (lane_id() == 0) segt[k] = make_uint2(pos, count);
+  if (!ring.drain()) ok = false;
+  if (lane_id() == 0) segt[0] = make_uint2(ok ? 1u : 0u, 0u);
 }
 
 // Plain kernels with one warp per chunk: Deflate (FAMILY 3), byte /

@@ -90,6 +90,11 @@ struct Args {
   int deferred_only;         // one-warp Deflate kernel: decode only chunks whose status is kDeferred
   uint32_t split_lg;         // batch kernel: RLE split rule (bucket_parts)
   uint32_t split_max;
+  // plain RLE v2 with a separate walk pass: kMaxSeg entries per chunk (see
+  // rle_seg_count); entry 0 .x = 1 when the walk pass wrote the chunk's
+  // segment starts, entries k = 1 .. nseg-1 = (stream position, value index)
+  uint2* seg;
+  int parts;  // warps per CTA of the decode pass the walk pass serves
 };
 
 // Batch scratch: [0] task counter, [1..128] bucket histogram, [129..256]
@@ -138,6 +143,10 @@ __global__ void rle_v1_kernel(Args a);
 __global__ void rle_v1_sizes_kernel(Args a);
 __global__ void rle_v2_kernel(Args a);
 __global__ void rle_v2_sizes_kernel(Args a);
+// Walk pass of the plain RLE v2 call: one warp per chunk (kWarpsPerBlock per
+// CTA) walks the run headers of every chunk that the decode pass stages
+// whole and writes its segment starts to a.seg.
+__global__ void rle_v2_walk_kernel(Args a);
 __global__ void inflate_kernel(Args a);
 __global__ void inflate_sizes_kernel(Args a);
 

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(512) byte_rle_cta_kernel(Args a) { rle_cta_bod
 __global__ void __launch_bounds__(512) rle_v2_sizes_kernel(Args a) {
   rle_cta_body<2, false>(a, a.stage_bytes);
 }
+__global__ void __launch_bounds__(kThreads) rle_v2_walk_kernel(Args a) { rle_v2_walk_body(a); }
 
 // this unit's copy of the work-wait bound (codag_set_wait_limit_ns)
 cudaError_t set_wait_limit_rle(uint64_t ns) { return set_wait_limit_here(ns); }

@@ -14,8 +14,10 @@
 //     staging ring, a byte swap and two shifts (any width <= 64 fits: widths
 //     that are not multiples of 8 are <= 30 bits);
 //   - PATCHED_BASE patch entries are decoded one per lane, their positions
-//     are a warp prefix sum of the gaps, and a 512-bit shared bitmap marks
-//     the patched values for the unpack loop;
+//     are a warp prefix sum of the gaps; a run of values up to 25 bits is
+//     unpacked like a DIRECT run and each patch-holding lane then rewrites
+//     its value, wider runs mark patched values in a 512-bit shared bitmap
+//     for the unpack loop;
 //   - DELTA runs are a warp-wide inclusive prefix sum per 32 deltas
 //     (__shfl_up_sync), carried across pieces;
 //   - outputs are coalesced 8-byte stores.
@@ -300,7 +302,29 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
       const bool bad = real && (ppos >= len || (before != 0 && ppos <= prev_pos));
       if (__ballot_sync(FULL, bad)) return part_error(ST_BAD_HEADER, pos, count);
       if (count > cap_values || len > cap_values - count) return part_error(ST_OVERFLOW, pos, count);
-      if (STORE) {
+      if (STORE && w <= 25) {
+        // the whole run is resident: unpack it like a DIRECT run (two values
+        // per lane and step, 32-bit arithmetic), then each lane that holds a
+        // patch rewrites its one patched value (after the warp's stores)
+        if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
+        uint64_t* o = out + count;
+        const uint32_t sec32 = (uint32_t)r.sec;
+        const uint32_t step = 32u * (uint32_t)w;
+        uint32_t bit = lane * (uint32_t)w;
+        uint32_t i = lane;
+        for (; i + 32 < len; i += 64, bit += 2 * step) {
+          const uint32_t va = v2_unpack32(in, sec32, bit, w);
+          const uint32_t vb = v2_unpack32(in, sec32, bit + step, w);
+          o[i] = base + va;
+          o[i + 32] = base + vb;
+        }
+        if (i < len) o[i] = base + v2_unpack32(in, sec32, bit, w);
+        __syncwarp();
+        if (real) o[ppos] = base + ((uint64_t)v2_unpack32(in, sec32, ppos * (uint32_t)w, w) | (patch << w));
+        __syncwarp();
+      } else if (STORE) {
+        // wide values stream through the ring 32 at a time: patches are
+        // merged in the unpack loop through a 512-bit bitmap of positions
         if (lane < 16) bitmap[lane] = 0;
         __syncwarp();
         if (real) {
@@ -310,18 +334,13 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
         __syncwarp();
         uint32_t carry = 0;
         uint64_t* o = out + count;
-        const bool narrow = w <= 25;
-        if (narrow && !in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
         for (uint32_t i0 = 0; i0 < len; i0 += 32) {
-          if (!narrow) {
-            const int64_t lo = r.sec + (((int64_t)i0 * w) >> 3);
-            if (!in.ensure(lo, lo + 4 * w + 16)) return part_error(ST_TIMEOUT, 0, count);
-          }
+          const int64_t lo = r.sec + (((int64_t)i0 * w) >> 3);
+          if (!in.ensure(lo, lo + 4 * w + 16)) return part_error(ST_TIMEOUT, 0, count);
           const uint32_t word = bitmap[i0 >> 5];
           const uint32_t i = i0 + lane;
           if (i < len) {
-            uint64_t v = narrow ? (uint64_t)v2_unpack32(in, (uint32_t)r.sec, i * (uint32_t)w, w)
-                                : v2_unpack(in, r.sec, i, w);
+            uint64_t v = v2_unpack(in, r.sec, i, w);
             if ((word >> lane) & 1u) {
               const uint64_t pv = pvals[carry + __popc(word & lanemask_lt())];
               if (w < 64) v |= pv << w;

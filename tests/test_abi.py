@@ -139,6 +139,20 @@ def test_batch_split_selection():
         codag.codag_set_batch_split(0, 0)
 
 
+def test_walk_pass_setting():
+    L = codag.lib()
+    assert codag.codag_get_walk_pass(2) == 0 and codag.codag_get_walk_pass(5) == 0  # default
+    assert codag.codag_get_walk_pass(1) == -1 and codag.codag_get_walk_pass(3) == -1
+    assert L.codag_set_walk_pass(1, 0) == codag.CODAG_EINVAL
+    assert L.codag_set_walk_pass(2, 2) == codag.CODAG_EINVAL
+    try:
+        codag.codag_set_walk_pass(5, 1)
+        assert codag.codag_get_walk_pass(2) == 1
+    finally:
+        codag.codag_set_walk_pass(2, 0)
+    assert codag.codag_get_walk_pass(2) == 0
+
+
 def test_deflate_pool_limit_setting():
     assert codag.codag_get_deflate_pool_limit() == 0  # default: no bound
     codag.codag_set_deflate_pool_limit(1 << 20)
