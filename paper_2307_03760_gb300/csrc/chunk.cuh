@@ -284,6 +284,8 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
                              published);
         else if (FAMILY == 4)
           byte_rle_walk(in, g.n_in, target, (int)nseg - 1, split_pos, split_cnt, published);
+        else if (cap_v < (1ull << 32))
+          rle_v2_walk_lean(in, (uint32_t)g.n_in, target, nseg, split_pos, split_cnt, published);
         else
           rle_v2_walk_staged(in, (uint32_t)g.n_in, target, (int)nseg - 1, split_pos, split_cnt,
                              published);

@@ -62,6 +62,23 @@ __device__ __forceinline__ uint32_t v2_unpack32(const In& in, uint32_t sec, uint
   return (x << (bit & 7)) >> (32 - w);
 }
 
+// Four consecutive w-bit fields (w <= 14) starting at bit `bit` of a packed
+// section at chunk position sec: one unaligned 8-byte read; after the
+// sub-byte shift 57 bits remain, enough for 4 x 14.  The first two fields are
+// the top 2w bits of the high word, the last two the top 2w bits of the word
+// that starts 2w bits further on.
+template <class In>
+__device__ __forceinline__ void v2_unpack4(const In& in, uint32_t sec, uint32_t bit, int w, uint32_t& v0,
+                                           uint32_t& v1, uint32_t& v2, uint32_t& v3) {
+  const uint64_t x = load_be64(in, sec + (bit >> 3)) << (bit & 7);
+  const uint32_t hi = (uint32_t)(x >> 32);
+  const uint32_t mid = (uint32_t)(x >> (32 - 2 * w));
+  v0 = hi >> (32 - w);
+  v1 = (hi << w) >> (32 - w);
+  v2 = mid >> (32 - w);
+  v3 = (mid << w) >> (32 - w);
+}
+
 __device__ __forceinline__ uint64_t unzigzag32(uint32_t v) {
   return (uint64_t)(int64_t)(int32_t)((v >> 1) ^ (0u - (v & 1u)));
 }
@@ -243,6 +260,75 @@ __device__ __forceinline__ void rle_v2_walk_staged(const In& in, uint32_t n_in, 
   for (; k <= nsplit; k++) publish_split(k, pos, count, split_pos, split_cnt, published);
 }
 
+// Width of a 5-bit width code, in four integer operations.
+__device__ __forceinline__ uint32_t v2_width_u(uint32_t code) {
+  const uint32_t wide = code < 27u ? 2u * code - 22u : 8u * code - 184u;
+  return code < 24u ? code + 1u : wide;
+}
+
+// The staged walk of rle_v2_walk_staged with every step in 32-bit arithmetic
+// straight from the stage words: the walk is one dependent chain per chunk
+// (the critical path of its CTA), so each run costs as few dependent
+// instructions as the header allows.  Same splits, same stop rule (a DELTA
+// varint that v2_run_extent could not size ends the walk).  Needs value
+// counts below 2^32 (targets in 32 bits).
+__device__ __forceinline__ void rle_v2_walk_lean(const StagedInput& in, uint32_t n_in,
+                                                 const uint64_t* target, uint32_t nseg,
+                                                 int64_t* split_pos, uint64_t* split_cnt,
+                                                 volatile uint32_t* published) {
+  const uint8_t* buf = in.buf;
+  const uint32_t skew = (uint32_t)in.skew;
+  uint32_t pos = 0, count = 0, k = 1;
+  uint32_t tk = (uint32_t)target[1];
+  while (pos < n_in) {
+    if (count >= tk) {
+      do {
+        publish_split((int)k, pos, count, split_pos, split_cnt, published);
+        if (++k >= nseg) return;
+        tk = (uint32_t)target[k];
+      } while (count >= tk);
+    }
+    const uint32_t r = pos + skew;
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(buf + (r & ~3u));
+    const uint32_t h = __funnelshift_r(wp[0], wp[1], (r & 3u) << 3);  // bytes pos .. pos+3
+    const uint32_t enc = (h >> 6) & 3u;
+    uint32_t len, ext;
+    if (enc == 0) {  // SHORT_REPEAT: header + value bytes
+      len = (h & 7u) + 3u;
+      ext = ((h >> 3) & 7u) + 2u;
+    } else {
+      len = (((h & 1u) << 8) | ((h >> 8) & 0xffu)) + 1u;
+      const uint32_t code = (h >> 1) & 31u;
+      if (enc == 1) {  // DIRECT
+        ext = 2u + ((len * v2_width_u(code) + 7u) >> 3);
+      } else if (enc == 2) {  // PATCHED_BASE
+        const uint32_t b2 = (h >> 16) & 0xffu, b3 = h >> 24;
+        const uint32_t ew = (uint32_t)v2_closest_fixed_bits((int)((b3 >> 5) + 1u + v2_width_u(b2 & 31u)));
+        ext = 4u + (b2 >> 5) + 1u + ((len * v2_width_u(code) + 7u) >> 3) + (((b3 & 31u) * ew + 7u) >> 3);
+      } else {  // DELTA: header, two varints, packed deltas
+        const uint64_t x = in.u64(pos + 2);
+        const uint64_t t1 = ~x & 0x8080808080808080ull;
+        const uint64_t t2 = t1 & (t1 - 1);
+        uint32_t vb;
+        if (t2) {
+          vb = (uint32_t)(__ffsll((long long)t2) >> 3);
+        } else {  // longer than the 8-byte window
+          uint64_t v;
+          int l1, l2;
+          if (varint_at(in, pos + 2, (int64_t)n_in - (pos + 2), &v, &l1) != ST_OK) break;
+          if (varint_at(in, pos + 2 + l1, (int64_t)n_in - (pos + 2 + l1), &v, &l2) != ST_OK) break;
+          vb = (uint32_t)(l1 + l2);
+        }
+        const uint32_t w = code == 0 ? 0u : v2_width_u(code);
+        ext = 2u + vb + ((w != 0 && len >= 2) ? (((len - 2u) * w + 7u) >> 3) : 0u);
+      }
+    }
+    count += len;
+    pos += ext;
+  }
+  for (; k < nseg; k++) publish_split((int)k, pos, count, split_pos, split_cnt, published);
+}
+
 // Decode part of one RLE v2 chunk.  The part's stream starts at a run
 // boundary (position 0 of `in`, n_in bytes to the chunk end) whose first
 // value index is count0; it decodes every run that starts before value hi_v
@@ -360,7 +446,37 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
           if (is_signed) v = unzigzag(v);
           if (lane < len) o[lane] = v;
         } else if (r.enc == 1) {  // DIRECT
-          if (w <= 25) {  // whole run resident at once (<= 1600 bytes), 32-bit unpack
+          if (w <= 14) {  // whole run resident; four values per lane from one 8-byte read
+            if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
+            const uint32_t sec32 = (uint32_t)r.sec;
+            uint32_t i0 = 0;
+            // lane l takes values i0 + 4l .. i0 + 4l + 3 and stores them with two
+            // 16-byte stores; the first value goes alone when that aligns them
+            if (reinterpret_cast<uintptr_t>(o) & 8) {
+              const uint32_t v = v2_unpack32(in, sec32, 0, w);
+              if (lane == 0) o[0] = is_signed ? unzigzag32(v) : (uint64_t)v;
+              i0 = 1;
+            }
+            for (; i0 < len; i0 += 128) {
+              const uint32_t i = i0 + 4 * lane;
+              if (i < len) {
+                uint32_t a0, a1, a2, a3;
+                v2_unpack4(in, sec32, i * (uint32_t)w, w, a0, a1, a2, a3);
+                const uint64_t x0 = is_signed ? unzigzag32(a0) : (uint64_t)a0;
+                const uint64_t x1 = is_signed ? unzigzag32(a1) : (uint64_t)a1;
+                const uint64_t x2 = is_signed ? unzigzag32(a2) : (uint64_t)a2;
+                const uint64_t x3 = is_signed ? unzigzag32(a3) : (uint64_t)a3;
+                if (i + 3 < len) {
+                  *reinterpret_cast<ulonglong2*>(o + i) = make_ulonglong2(x0, x1);
+                  *reinterpret_cast<ulonglong2*>(o + i + 2) = make_ulonglong2(x2, x3);
+                } else {
+                  o[i] = x0;
+                  if (i + 1 < len) o[i + 1] = x1;
+                  if (i + 2 < len) o[i + 2] = x2;
+                }
+              }
+            }
+          } else if (w <= 25) {  // whole run resident at once (<= 1600 bytes), 32-bit unpack
             if (!in.ensure(r.sec, r.sec + r.nbytes + 8)) return part_error(ST_TIMEOUT, 0, count);
             const uint32_t sec32 = (uint32_t)r.sec;
             const uint32_t step = 32u * (uint32_t)w;
@@ -417,6 +533,40 @@ __device__ PartResult rle_v2_part(In& in, uint8_t* scratch, int64_t n_in, bool i
                 if (lane == 0) od[0] = carry;
                 j0 = 1;
               }
+              // deltas of <= 14 bits: four per lane from one 8-byte read, one
+              // scan per 128 deltas (their sum stays below 2^21), two 16-byte
+              // stores per lane
+              if (w <= 14)
+                for (; j0 < nd; j0 += 128) {
+                  const uint32_t j = j0 + 4 * lane;
+                  uint32_t d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+                  if (j < nd) {
+                    v2_unpack4(in, sec32, j * (uint32_t)w, w, d0, d1, d2, d3);
+                    const uint32_t left = nd - j;
+                    if (left < 4) {
+                      d3 = 0;
+                      if (left < 3) d2 = 0;
+                      if (left < 2) d1 = 0;
+                    }
+                  }
+                  const uint32_t sum = d0 + d1 + d2 + d3;
+                  const uint32_t incl = warp_incl_scan32(sum);
+                  const uint32_t p0 = incl - sum + d0, p1 = p0 + d1, p2 = p1 + d2;
+                  const uint64_t s0 = negative ? carry - (uint64_t)p0 : carry + (uint64_t)p0;
+                  const uint64_t s1 = negative ? carry - (uint64_t)p1 : carry + (uint64_t)p1;
+                  const uint64_t s2 = negative ? carry - (uint64_t)p2 : carry + (uint64_t)p2;
+                  const uint64_t s3 = negative ? carry - (uint64_t)incl : carry + (uint64_t)incl;
+                  if (j + 3 < nd) {
+                    *reinterpret_cast<ulonglong2*>(od + j) = make_ulonglong2(s0, s1);
+                    *reinterpret_cast<ulonglong2*>(od + j + 2) = make_ulonglong2(s2, s3);
+                  } else if (j < nd) {
+                    od[j] = s0;
+                    if (j + 1 < nd) od[j + 1] = s1;
+                    if (j + 2 < nd) od[j + 2] = s2;
+                  }
+                  const uint64_t tot = __shfl_sync(FULL, incl, 31);
+                  carry = negative ? carry - tot : carry + tot;
+                }
               for (; j0 < nd; j0 += 64) {
                 const uint32_t j = j0 + 2 * lane;
                 uint32_t da = 0, db = 0;
