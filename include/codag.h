@@ -113,8 +113,9 @@ enum {
  * to a library pool (about a quarter of the decoded size; see
  * codag_set_deflate_pool_limit), then the LZ77 copies with one warp per
  * chunk writing 32 consecutive output bytes per step; a chunk whose
- * commands do not fit its part of the pool is decoded by one warp instead
- * (the same result).  Output is written with coalesced stores.
+ * commands do not fit its part of the pool, or whose output span is over
+ * 128 KiB (one lane would hold the pass back), is decoded by one warp
+ * instead (the same result).  Output is written with coalesced stores.
  *
  * format        one of codag_format.
  * comp, comp_offsets, out, out_offsets: see the layout above (device).

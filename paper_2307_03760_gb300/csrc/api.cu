@@ -403,10 +403,15 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     const unsigned g1 = (unsigned)((n + lanes - 1) / lanes < (uint64_t)w->sm_count ? (n + lanes - 1) / lanes
                                                                                    : (uint64_t)w->sm_count);
     if (!store) {
+      // then the one-warp sizes kernel for the chunks the lanes left to it
       inflate_huffman_sizes_kernel<<<g1, 32 * kHufWarps, kHufSmem, stream>>>(a, h);
+      Args b = a;
+      b.deferred_only = 1;
+      inflate_sizes_kernel<<<(unsigned)((n + kWarpsPerBlock - 1) / kWarpsPerBlock), kThreads,
+                             kWarpsPerBlock * kDeflateWarp, stream>>>(b);
       e = cudaGetLastError();
       if (e != cudaSuccess) return cuda_fail(e, "decode launch");
-      g_launches.fetch_add(1);
+      g_launches.fetch_add(2);
       return CODAG_OK;
     }
     inflate_huffman_kernel<<<g1, 32 * kHufWarps, kHufSmem, stream>>>(a, h);

@@ -62,6 +62,15 @@ constexpr int kFixLTB = 9;    // lit/len table index bits of the fixed code (eve
 constexpr int kLaneDTB = 7;   // distance (and code-length) table index bits
 constexpr int kHufWarps = 4;  // warps per CTA of the Huffman kernel (one CTA per SM)
 constexpr int kLz77Warps = 8;  // warps per CTA of the copy kernel
+// Chunks that decode to more than this are left to the one-warp decoder
+// (kDeferred): one lane decodes a chunk at about the speed of one warp, so a
+// few long chunks would hold the whole Huffman pass (a 1 MiB chunk on one
+// lane takes some 150 ms), while the one-warp pass runs them with the SM to
+// fewer decoders.
+constexpr uint32_t kHufMaxOut = 128u * 1024u;
+// The sizes pass knows no output span: it leaves chunks of more compressed
+// bytes than this to the one-warp decoder instead.
+constexpr uint64_t kHufMaxInSizes = 64u * 1024u;
 
 // Table entry (16 bits): bits 0-3 code length, 4-12 value, 13-15 kind.
 // Values: a literal byte; a code-length symbol; a length symbol as index
@@ -375,6 +384,10 @@ struct LaneDec {
         return;
       }
       cap = (uint32_t)(oe - os);
+      if (cap > kHufMaxOut) {
+        finish(kDeferred);
+        return;
+      }
       out = a->out + os;
       // the region of a chunk with a valid span; one past the pool (or an
       // output start before the launch's first) leaves the chunk to the
@@ -394,6 +407,10 @@ struct LaneDec {
     }
     if (n_in >= (1ull << 29)) {
       finish(ST_BAD_SPAN);
+      return;
+    }
+    if (!STORE && n_in > kHufMaxInSizes) {
+      finish(kDeferred);
       return;
     }
     const uint8_t* chunk = a->comp + cs;

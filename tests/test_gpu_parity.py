@@ -92,6 +92,19 @@ def test_deflate_pool_bound_fallback(limit):
     assert (st == 0).sum() >= w.n // 2
 
 
+def test_deflate_long_chunks_beside_short_ones():
+    """Chunks whose output span is over 128 KiB go to the one-warp decoder
+    after the two passes; those at or under it stay in the passes."""
+    sizes = [4096, 131072, 131073, 700000, 65536, 131072 + 4096, 1000, 300000]
+    w = synth.build_chunks([3] * len(sizes), sizes, seed=91)
+    got, st = run_plain(3, w.comp, w.comp_off, w.out_off)
+    assert (st == 0).all()
+    assert_parity(3, w.comp, w.comp_off, w.out_off, got, st)
+    # the sizes pass leaves chunks of over 64 KiB compressed to one warp
+    sz, sst = run_sizes(3, w.comp, w.comp_off)
+    assert (sst == 0).all() and np.array_equal(sz, np.array(sizes, np.uint64))
+
+
 @pytest.mark.parametrize("shift", [1, 3, 8, 15])
 def test_deflate_unaligned_output(shift):
     sizes = [65536, 1, 333, 65535, 20000]
