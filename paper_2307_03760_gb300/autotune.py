@@ -40,14 +40,18 @@ SPLIT_RULES = [(s, m) for s in (13, 14, 15, 16, 17, 18) for m in (8, 16, 32)] + 
 BATCH_CTAS = [1, 2, 3, 4, 5, 6, 8, 9]
 
 
-def sweep(run, candidates, setter, reps: int = 7, warmup: int = 2, timer=None) -> dict:
+def sweep(run, candidates, setter, reps: int = 7, warmup: int = 2, timer=None, sync=None) -> dict:
     """Time `run()` for every candidate (set through `setter`); returns
-    {candidate: [ms, ...]}."""
+    {candidate: [ms, ...]}.  sync (if given) runs after each warm-up call, so
+    that what a call learns for the next one (the Deflate command pool size)
+    is in place before the timed calls."""
     out = {}
     for c in candidates:
         setter(c)
         for _ in range(warmup):
             run()
+            if sync:
+                sync()
         out[c] = [timer(run) for _ in range(reps)]
     return out
 
@@ -152,19 +156,25 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1, only_batch: bool = False) -> 
         comp, coff, ooff, _, out, _ = upload(w)
         fmt = int(w.formats[0])
         run = lambda: codag.codag_decompress(fmt, comp, coff, w.n, out, ooff)  # noqa: E731
-        t = sweep(run, list(range(1, 17)), codag.codag_set_parts_per_chunk, timer=timer)
+        t = sweep(run, list(range(1, 17)), codag.codag_set_parts_per_chunk, timer=timer,
+                  sync=torch.cuda.synchronize)
         best, ms = choose(t)
         table["rle_parts"][name] = {"chunks": w.n, "best": best, "ms": round(ms, 4)}
         table["sweeps"][f"{name}_parts"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}
     codag.codag_set_parts_per_chunk(0)
-    # input staging of the one-warp-per-chunk decoders (0: shared ring, 1: registers)
+    # input staging of Deflate (0: two passes, 1: one warp per chunk through a
+    # register ring) and byte RLE (0: shared ring, 1: registers), on the full
+    # columns: the Huffman pass gives each chunk one lane, so it needs tens of
+    # thousands of chunks to fill the GPU, and a smaller column would favour
+    # the one-warp decoder
     table["input_staging"] = {}
-    for name, w in (("deflate", synth.deflate_column(seed, total=256 * synth.MiB)),
+    for name, w in (("deflate", synth.deflate_column(seed)),
                     ("byte_rle", synth.byte_rle_column(seed))):
         comp, coff, ooff, _, out, _ = upload(w)
         fmt = int(w.formats[0])
         run = lambda: codag.codag_decompress(fmt, comp, coff, w.n, out, ooff)  # noqa: E731
-        t = sweep(run, [0, 1], lambda m: codag.codag_set_input_staging(fmt, m), reps=5, timer=timer)
+        t = sweep(run, [0, 1], lambda m: codag.codag_set_input_staging(fmt, m), reps=5, timer=timer,
+                  sync=torch.cuda.synchronize)
         best, ms = choose(t)
         table["input_staging"][name] = {"format": fmt, "best": best, "ms": round(ms, 4)}
         table["sweeps"][f"{name}_input_staging"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}

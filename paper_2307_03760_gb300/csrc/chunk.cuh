@@ -145,14 +145,15 @@ __device__ __forceinline__ PartResult decode_part(Ring& ring, uint8_t* scratch, 
 }
 
 // Wait (bounded by work_wait_ns()) until at least k + 1 segment starts are
-// published.
-__device__ __forceinline__ bool wait_published(volatile uint32_t* published, uint32_t k) {
+// published, napping nap_ns between looks.
+__device__ __forceinline__ bool wait_published(volatile uint32_t* published, uint32_t k,
+                                               uint32_t nap_ns = 128) {
   if (*published > k) return true;
   const uint64_t limit = work_wait_ns();
   if (limit == 0) return false;
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t polls = 0; polls < kMaxWaitPolls; polls++) {
-    __nanosleep(128);
+    __nanosleep(nap_ns);
     if (*published > k) return true;
     if (globaltimer_ns() - t0 > limit) return false;
   }
@@ -296,7 +297,10 @@ __device__ __forceinline__ void rle_cta_body(const Args& a, int stage_bytes) {
         k = __shfl_sync(FULL, k, 0);
         if (k >= nseg) break;
         PartResult r;
-        if (!wait_published(published, k)) {
+        // byte RLE: a segment start comes about every 130 control bytes of
+        // a serial walk, so a longer nap costs no latency and spares the
+        // walker's issue slots
+        if (!wait_published(published, k, FAMILY == 4 ? 1024u : 128u)) {
           r = PartResult{ST_TIMEOUT, 0, 0};
         } else {
           __threadfence_block();

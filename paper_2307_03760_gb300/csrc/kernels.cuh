@@ -46,7 +46,7 @@ constexpr int kRleStageBytes = 32768 + 256;
 constexpr int kMaxSeg = 64;
 constexpr int kSegValues = 1024;
 constexpr int kSegValuesV1 = 256;  // RLE v1: a cheap walk, so finer segments
-constexpr int kSegBytesByteRle = 4096;  // byte / boolean RLE: decoded bytes per segment
+constexpr int kSegBytesByteRle = 2048;  // byte / boolean RLE: decoded bytes per segment
 // per-CTA extras: mbarrier, status key, published/claimed, split positions,
 // counts and targets
 constexpr int kRleCtaExtra = 24 + 3 * (kMaxSeg + 1) * 8;
