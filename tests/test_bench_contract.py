@@ -35,7 +35,7 @@ def test_reference_line(workload):
 def test_committed_traffic_entries():
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         t = json.load(f)
-    for kernel in ("rle_v2_kernel", "rle_v1_kernel", "inflate_kernel", "batch_kernel"):
+    for kernel in ("rle_v2_kernel", "rle_v1_kernel", "inflate_huffman_kernel", "inflate_lz77_kernel", "batch_kernel"):
         e = t[kernel]
         assert e["dram_bytes"] == e["dram_read"] + e["dram_write"] > 0
         assert e["units"] > 0 and e["workload"] and e["command"].startswith("ncu ")
