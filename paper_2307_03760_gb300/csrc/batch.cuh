@@ -11,7 +11,7 @@ namespace codag {
 // first); an RLE chunk of bucket b is cut into bucket_parts(b) parts, each
 // decoded by the warp that claims it after walking to the part's start.
 template <class Ring>
-__global__ void __launch_bounds__(kThreads) batch_kernel(Args a) {
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(Args a) {
   static_assert(Ring::MAX_SPAN >= kRleMinSpan, "batch ring too shallow for the RLE decoders");
   constexpr int kWarpBytes = batch_warp_bytes<Ring>();
   extern __shared__ __align__(128) uint8_t smem[];
