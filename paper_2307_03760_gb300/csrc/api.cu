@@ -399,9 +399,9 @@ codag_status launch_kernel(const Workspace& ws, int format, const void* comp,
     HufArgs h{dr->cmd, dr->pool_words, dr->ncmd, dr->counter, dr->need};
     cudaError_t e = cudaMemsetAsync(dr->counter, 0, sizeof(uint32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
-    const uint64_t lanes = 32ull * kHufWarps;
-    const unsigned g1 = (unsigned)((n + lanes - 1) / lanes < (uint64_t)w->sm_count ? (n + lanes - 1) / lanes
-                                                                                   : (uint64_t)w->sm_count);
+    // one CTA per SM (fewer for fewer chunks than SMs): the lanes' first
+    // chunks are spread over every warp
+    const unsigned g1 = (unsigned)(n < (uint64_t)w->sm_count ? n : (uint64_t)w->sm_count);
     if (!store) {
       // then the one-warp sizes kernel for the chunks the lanes left to it
       inflate_huffman_sizes_kernel<<<g1, 32 * kHufWarps, kHufSmem, stream>>>(a, h);

@@ -318,6 +318,7 @@ struct LaneDec {
   uint32_t ncmd;
   uint32_t ccap;  // command words of the chunk's slot
   bool stuck;     // the fast step met a symbol it leaves to step()
+  bool first;     // the lane has not claimed a chunk yet
   uint8_t* out;
   uint32_t* cmd;
   const uint16_t* lt;  // lit/len table, element stride ls, index mask lm
@@ -353,9 +354,19 @@ struct LaneDec {
     state = LS_NEED_CHUNK;
   }
 
-  // Take the next chunk (state LS_NEED_CHUNK).
+  // Take the next chunk (state LS_NEED_CHUNK).  A lane's first chunk is
+  // fixed: lane l of warp w (of W in the grid) takes chunk l * W + w, so a
+  // call with fewer chunks than lanes spreads them over every warp (fewer
+  // lanes per warp diverge less and each chunk's chain advances faster);
+  // later chunks come from the counter, past the first 32 W.
   __device__ void claim() {
-    c = atomicAdd(h->counter, 1u);
+    const uint32_t W = gridDim.x * (blockDim.x >> 5);
+    if (first) {
+      first = false;
+      c = (uint64_t)lane * W + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    } else {
+      c = 32ull * W + atomicAdd(h->counter, 1u);
+    }
     if (c >= a->n) {
       state = LS_GONE;
       return;
@@ -706,6 +717,7 @@ __device__ void huffman_body(const Args& a, const HufArgs& h) {
   s.F = F;
   s.lane = lane_id();
   s.state = LS_NEED_CHUNK;
+  s.first = true;
   for (;;) {
     while (s.state == LS_NEED_CHUNK) s.claim();
     if (__all_sync(FULL, s.state == LS_GONE)) break;
