@@ -24,15 +24,44 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuning_gb300.json")
 
 
-def choose(timings: dict) -> tuple:
-    """Fastest candidate by median time; ties go to the smaller value
-    (fewer warps per chunk / fewer CTAs per SM leave more room to others)."""
-    best = None
-    for cand, times in sorted(timings.items()):
-        m = statistics.median(times)
-        if best is None or m < best[1] * (1 - 1e-9):
-            best = (cand, m)
-    return best
+def choose(timings: dict, rel_tol: float = 0.01) -> tuple:
+    """(candidate, its median time): the fastest by median, where candidates
+    within rel_tol of the fastest count as ties, which go to the smallest
+    candidate (fewer warps per chunk or CTAs per SM leave room to others,
+    and settings that launch the same thing, such as CTA counts above what
+    fits on an SM, only differ by noise)."""
+    med = {c: statistics.median(t) for c, t in timings.items()}
+    m0 = min(med.values())
+    for c in sorted(med):
+        if med[c] <= m0 * (1 + rel_tol):
+            return c, med[c]
+
+
+def _unkey(k: str):
+    return tuple(int(v) for v in k.split("x")) if "x" in k else int(k)
+
+
+def reselect(table: dict) -> dict:
+    """Recompute a table's choices from its recorded sweeps (medians, ms)
+    with `choose`; tune() ends with this, and it re-applies a changed
+    selection rule to measurements already taken."""
+    sw = table.get("sweeps", {})
+    for name, e in table.get("rle_parts", {}).items():
+        if f"{name}_parts" in sw:
+            c, ms = choose({_unkey(k): [v] for k, v in sw[f"{name}_parts"].items()})
+            e["best"], e["ms"] = c, round(ms, 4)
+    for name, e in table.get("input_staging", {}).items():
+        if f"{name}_input_staging" in sw:
+            c, ms = choose({_unkey(k): [v] for k, v in sw[f"{name}_input_staging"].items()})
+            e["best"], e["ms"] = c, round(ms, 4)
+    if "batch_staging_x_ctas" in sw and "staging_depth" in table:
+        (slot, slots, ctas), ms = choose({_unkey(k): [v] for k, v in sw["batch_staging_x_ctas"].items()})
+        table["staging_depth"].update(best=[slot, slots], ms=round(ms, 3))
+        table["batch_ctas_per_sm"].update(best=ctas, ms=round(ms, 3))
+    if "batch_split" in sw and "chunk_mapping" in table:
+        (lg, mx), ms = choose({_unkey(k): [v] for k, v in sw["batch_split"].items()})
+        table["chunk_mapping"].update(best=[lg, mx], ms=round(ms, 3))
+    return table
 
 
 # RLE split rules offered to the batch sweep: (split_log2, max_parts)
@@ -147,6 +176,7 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1, only_batch: bool = False) -> 
         table.setdefault("sweeps", {})
         table["device"] = torch.cuda.get_device_name(0)
         tune_batch(table, seed)
+        reselect(table)
         with open(path, "w") as f:
             json.dump(table, f, indent=1)
         return table
@@ -180,6 +210,7 @@ def tune(path: str = DEFAULT_TABLE, seed: int = 1, only_batch: bool = False) -> 
         table["sweeps"][f"{name}_input_staging"] = {str(k): round(statistics.median(v), 4) for k, v in t.items()}
         codag.codag_set_input_staging(fmt, 0)
     tune_batch(table, seed)
+    reselect(table)
     with open(path, "w") as f:
         json.dump(table, f, indent=1)
     return table
@@ -223,5 +254,12 @@ def apply(path: str = DEFAULT_TABLE, n_chunks: int | None = None, family: str = 
 if __name__ == "__main__":
     import sys
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    print(json.dumps(tune(args[0] if args else DEFAULT_TABLE, only_batch="--only-batch" in sys.argv),
-                     indent=1))
+    path = args[0] if args else DEFAULT_TABLE
+    if "--reselect" in sys.argv:  # no GPU: re-apply `choose` to the recorded sweeps
+        with open(path) as f:
+            t = reselect(json.load(f))
+        with open(path, "w") as f:
+            json.dump(t, f, indent=1)
+        print(json.dumps({k: v for k, v in t.items() if k != "sweeps"}, indent=1))
+    else:
+        print(json.dumps(tune(path, only_batch="--only-batch" in sys.argv), indent=1))

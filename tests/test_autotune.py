@@ -102,3 +102,27 @@ def test_committed_table_entries_are_valid():
     assert len(table["sweeps"]["batch_staging_x_ctas"]) == \
         len(codag.codag_batch_staging_shapes()) * len(autotune.BATCH_CTAS)
     assert len(table["sweeps"]["batch_split"]) == len(autotune.SPLIT_RULES)
+
+
+def test_reselect_applies_choose_to_recorded_sweeps():
+    """Near-ties (within 1%) go to the smaller setting, from the medians a
+    tuning table records; no GPU involved."""
+    from paper_2307_03760_gb300 import autotune
+    table = {
+        "rle_parts": {"rle_v2": {"chunks": 10, "best": 0, "ms": 0}},
+        "input_staging": {"deflate": {"format": 3, "best": 1, "ms": 0}},
+        "staging_depth": {"best": [0, 0], "ms": 0}, "batch_ctas_per_sm": {"best": 0, "ms": 0},
+        "chunk_mapping": {"best": [0, 0], "ms": 0},
+        "sweeps": {
+            "rle_v2_parts": {"4": 0.999, "5": 0.995, "6": 0.990, "8": 1.2},
+            "deflate_input_staging": {"0": 12.5, "1": 29.5},
+            "batch_staging_x_ctas": {"1024x4x3": 76.0, "1024x4x8": 75.5, "2048x4x2": 80.0, "256x8x1": 130.0},
+            "batch_split": {"16x1": 72.6, "16x16": 72.9, "12x32": 79.0},
+        },
+    }
+    t = autotune.reselect(table)
+    assert t["rle_parts"]["rle_v2"]["best"] == 4  # 0.999 is within 1% of 0.990
+    assert t["input_staging"]["deflate"]["best"] == 0
+    assert t["staging_depth"]["best"] == [1024, 4] and t["batch_ctas_per_sm"]["best"] == 3
+    assert t["chunk_mapping"]["best"] == [16, 1]
+    assert autotune.choose({1: [1.0], 2: [0.95]})[0] == 2  # 5% apart: not a tie
