@@ -32,6 +32,9 @@ def _cases():
         (1, synth.build_chunks([1] * 12, [65536] * 10 + [big, 16], seed=52)),
         (6, synth.build_chunks([6] * 12, [65536] * 11 + [300000], seed=53)),
         (8, synth.orc_zlib_column(54, total=8 << 20)),
+        # a chunk over 128 KiB goes to the persistent one-warp pass after the
+        # two Deflate passes, whose ring waits can run out
+        (3, synth.build_chunks([3] * 7, [65536] * 6 + [300000], seed=56)),
     ]
 
 
@@ -46,7 +49,7 @@ def test_zero_wait_bound_gives_timeouts_only_then_exact_again():
             _, st = run_plain(fmt, w.comp, w.comp_off, w.out_off)
             assert set(np.unique(st).tolist()) <= {0, TIMEOUT}, (fmt, np.unique(st))
             timeouts += int((st == TIMEOUT).sum())
-            if fmt in (1, 2):  # the sizes walks wait for their staging too
+            if fmt in (1, 2, 3):  # the sizes walks (and the one-warp Deflate sizes) wait too
                 _, sst = run_sizes(fmt, w.comp, w.comp_off)
                 assert set(np.unique(sst).tolist()) <= {0, TIMEOUT}
         _, bst = run_batch(mixed.formats, mixed.comp, mixed.comp_off, mixed.out_off)
